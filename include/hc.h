@@ -1,0 +1,235 @@
+/*
+ * hc.h -- C ABI of libhc.so: batched approximate kNN over Hilbert-curve
+ * subindexes (Multicurves / Hypercurves, Teodoro et al., arXiv:1209.0410),
+ * GPU-resident on one NVIDIA GB300 (sm_103a).
+ *
+ * Vocabulary (the paper's notation):
+ *   B, n     database of n vectors of d coordinates (Algorithm 1 input)
+ *   curves   number of subindexes per partition; each curve c indexes the
+ *            dims_per_curve coordinates a[c][0..m) of every vector
+ *   C^-1     the Hilbert extended-key of a projection (Sec. 2.2.1): m
+ *            coordinates of 8 bits -> one key of 8m bits (at most 128)
+ *   p        probe depth per side: the search takes the p list entries below
+ *            the query key and the p at or above it (the paper's depth is 2p)
+ *   k        neighbours returned per query
+ *   l        partitions (Hypercurves, Sec. 4.1): the database is split into
+ *            l disjoint id ranges, each with its own curves sorted lists
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named *_dev are device pointers on the current CUDA device;
+ *     *_host are host pointers (pinned or pageable).  The caller owns every
+ *     buffer it passes in.  Row-major layouts throughout.
+ *   - cuda_stream is a cudaStream_t cast to void* (NULL = legacy default
+ *     stream).  Entry points taking device buffers are asynchronous on that
+ *     stream unless stated otherwise; results are valid once the stream
+ *     reaches the point of the call.
+ *   - Every entry point returns an hc_status; no C++ exception crosses the
+ *     ABI.  hc_strerror() names a status.  On an error return nothing has
+ *     been written to the caller's output buffers unless stated otherwise.
+ *   - Distances are squared Euclidean (Eq. 2 squared: same ranking).  uint8
+ *     data gives exact int32 distances; float32 data accumulates in float32.
+ *   - Results are ordered by ascending (distance, id): equal distances rank
+ *     the lower id first.  When fewer than k distinct candidates exist the
+ *     tail is padded with id -1 and distance INT32_MAX (uint8) or +inf
+ *     (float32).
+ *   - The Hilbert orientation is that of Skilling's transpose formulation
+ *     ("Programming the Hilbert curve", 2004): key bits are read level by
+ *     level from the top coordinate bit, axis 0 first.  Float32 coordinates
+ *     enter keys as (uint8)clamp(rint(x * 255f), 0, 255), decided in float32.
+ */
+#ifndef HC_H
+#define HC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HC_API __attribute__((visibility("default")))
+#else
+#define HC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- statuses */
+typedef enum {
+    HC_OK = 0,
+    HC_PENDING = 1,             /* hc_serve_poll: the request has not finished */
+    HC_ERR_ARG = -1,            /* an argument is out of range or inconsistent */
+    HC_ERR_OOM = -2,            /* a device or host allocation failed */
+    HC_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+    HC_ERR_BUDGET = -4,         /* admission refused: over the HBM budget */
+    HC_ERR_TIMEOUT = -5,        /* a host-side wait ran out of time */
+    HC_ERR_DEVICE_STATUS = -6,  /* a kernel reported an error status */
+    HC_ERR_STATE = -7           /* object used in the wrong state (e.g. an unknown ticket) */
+} hc_status;
+
+typedef enum { HC_U8 = 0, HC_F32 = 1 } hc_dtype;
+
+typedef struct hc_index hc_index;
+
+/* Index construction parameters (Algorithm 1 inputs B, curves, dims[], a). */
+typedef struct {
+    uint64_t n;                /* rows, 1 <= n < 2^31 and curves * n < 2^32 */
+    uint32_t d;                /* coordinates per row; rows must be a multiple
+                                  of 16 bytes (d % 16 == 0 for HC_U8,
+                                  d % 4 == 0 for HC_F32), d <= 4096 */
+    uint32_t curves;           /* subindexes per partition, 1..32 */
+    uint32_t dims_per_curve;   /* m, 1..16 (keys of 8m bits) */
+    uint32_t bits;             /* coordinate bits; must be 8 */
+    hc_dtype dtype;            /* HC_U8 or HC_F32 */
+    const uint32_t* dim_map;   /* HOST array a[c][j], curves*m entries, each < d;
+                                  NULL = consecutive dims (a[c][j] = c*m + j,
+                                  needs curves*m <= d).  Copied at build. */
+    uint32_t partitions;       /* l >= 1 (0 is read as 1); partition j holds
+                                  ids [floor(j*n/l), floor((j+1)*n/l));
+                                  l * curves <= 256 */
+} hc_build_params;
+
+/*
+ * hc_build -- Algorithm 1 on the GPU: for every partition and curve, the
+ * extended-key of each row's projection, then a stable device radix sort of
+ * (key, id), giving one list sorted by (key, id) per (partition, curve).
+ *   db_dev   n x d rows (uint8 or float32 per params->dtype), 16-byte aligned.
+ *            NOT copied: the index keeps the pointer, so the caller keeps the
+ *            buffer alive and unchanged until hc_free.
+ *   out      receives the new index (owned by the library; free with hc_free).
+ * The library allocates the index arrays (20 bytes per row and curve) and,
+ * during the call, scratch of about 44 bytes per row and curve; HC_ERR_OOM
+ * if that fails.  Asynchronous on cuda_stream; the index may be used by
+ * later work on the same stream (or after synchronising).
+ */
+HC_API int hc_build(const void* db_dev, const hc_build_params* params, void* cuda_stream,
+                    hc_index** out);
+
+/*
+ * hc_build_host -- as hc_build, but db_host is a HOST buffer: the library
+ * copies it into device memory it owns (freed by hc_free).  Returns once the
+ * index is complete on the device (synchronises cuda_stream).
+ */
+HC_API int hc_build_host(const void* db_host, const hc_build_params* params, void* cuda_stream,
+                         hc_index** out);
+
+/*
+ * hc_query -- Algorithm 2 for nq queries at once (queries grouped into one
+ * GPU batch, Sec. 5.1), fused into one kernel: per query, the extended-key
+ * of every curve's projection, lower_bound in each sorted list, the window
+ * [max(0, pos-p), min(n_list, pos+p)), exact distances of the window rows,
+ * and one running top-k over the union of all windows of all curves and
+ * partitions with duplicate ids dropped (the Aggregator's reduction of
+ * Sec. 4.1 folded into the selection).
+ *   q_dev         nq x d queries of the index's dtype, 16-byte aligned rows
+ *   k             1..128;  p: 0..2^30 (p = 0 gives all-padding results)
+ *   out_ids_dev   nq x k int32
+ *   out_dist_dev  nq x k int32 (HC_U8) or float (HC_F32)
+ * nq = 0 is a no-op.  No allocation; asynchronous on cuda_stream.
+ */
+HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
+                    int32_t* out_ids_dev, void* out_dist_dev, void* cuda_stream);
+
+/*
+ * hc_query_host -- hc_query from HOST buffers: copies the queries in, runs
+ * the query kernel and copies the results back, on cuda_stream, and returns
+ * once the results are in the host buffers.  Device staging buffers are
+ * owned by the index and grow on demand (HC_ERR_OOM if they cannot).
+ * Calls on the same index must not overlap (they share the staging).
+ */
+HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,
+                         int32_t* out_ids_host, void* out_dist_host, void* cuda_stream);
+
+/* hc_free -- releases an index and everything it owns (not db_dev).  The
+ * caller makes sure no work using the index is still queued.  NULL is ok. */
+HC_API void hc_free(hc_index* idx);
+
+/* hc_strerror -- static text for an hc_status value. */
+HC_API const char* hc_strerror(int status);
+
+/* ------------------------------------------------------- introspection */
+typedef struct {
+    uint64_t n;
+    uint32_t d, curves, dims_per_curve, partitions, lists;
+    hc_dtype dtype;
+    const uint64_t* keys_hi_dev;  /* lists concatenated, list L = part*curves + c */
+    const uint64_t* keys_lo_dev;  /* low 64 bits of each key */
+    const uint32_t* ids_dev;      /* row id of each entry */
+    const void* db_dev;
+} hc_index_info;
+
+/* hc_index_describe -- fills *info; the device arrays stay owned by idx.
+ * list_off_host (nullable) receives lists+1 offsets of the lists. */
+HC_API int hc_index_describe(const hc_index* idx, hc_index_info* info, uint64_t* list_off_host);
+
+/* hc_index_copy_lists -- copies the sorted lists (all lists concatenated,
+ * list_off order) into caller-owned device buffers of total = n * curves
+ * entries each.  Asynchronous on cuda_stream; no allocation. */
+HC_API int hc_index_copy_lists(const hc_index* idx, uint64_t* keys_hi_dev, uint64_t* keys_lo_dev,
+                               uint32_t* ids_dev, void* cuda_stream);
+
+/* ----------------------------------------------------- separate steps */
+
+/*
+ * hc_hilbert_keys -- the extended-key C^-1 of each vector's projection onto
+ * every curve (Sec. 2.2.1; the per-curve step of Algorithms 1 and 2).
+ *   x_dev        count x d vectors (dtype), 16-byte aligned rows
+ *   dim_map_host curves*m attribution, NULL = consecutive
+ *   hi_dev/lo_dev count x curves uint64 each: key = hi * 2^64 + lo
+ * Asynchronous on cuda_stream; allocates only a small copy of dim_map.
+ */
+HC_API int hc_hilbert_keys(const void* x_dev, hc_dtype dtype, uint64_t count, uint32_t d,
+                           uint32_t curves, uint32_t m, const uint32_t* dim_map_host,
+                           uint64_t* hi_dev, uint64_t* lo_dev, void* cuda_stream);
+
+/*
+ * hc_sort_keys -- stable LSD radix sort of (key, id) records by their 128-bit
+ * key, independently within each segment [seg_off[s], seg_off[s+1]) (the
+ * sorted lists of Algorithm 1).  Equal keys keep their input order, so ids
+ * that enter ascending leave ordered by (key, id).
+ *   hi_dev, lo_dev, ids_dev  total = seg_off_host[nseg] records, in place
+ *   seg_off_host             nseg+1 offsets (host), non-decreasing,
+ *                            total < 2^32
+ *   key_bits                 significant low bits of every key (1..128);
+ *                            digits above them are taken as zero and skipped
+ * Allocates scratch of 36 bytes per record for the call; synchronises
+ * cuda_stream before returning (the scratch is freed).
+ */
+HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
+                        const uint64_t* seg_off_host, uint32_t nseg, uint32_t key_bits,
+                        void* cuda_stream);
+
+/*
+ * hc_query_positions -- the lower_bound step of Algorithm 2 alone: for each
+ * query and list, the first entry whose key is >= the query's key.
+ *   pos_dev   nq x lists int64
+ */
+HC_API int hc_query_positions(hc_index* idx, const void* q_dev, uint32_t nq, int64_t* pos_dev,
+                              void* cuda_stream);
+
+/*
+ * hc_bruteforce -- exact kNN (Eq. 3) of nq queries over all n rows, same
+ * ordering, padding and distance arithmetic as hc_query.  Used as recall
+ * ground truth.  k: 1..128.  No allocation; asynchronous on cuda_stream.
+ */
+HC_API int hc_bruteforce(const void* db_dev, hc_dtype dtype, uint64_t n, uint32_t d,
+                         const void* q_dev, uint32_t nq, uint32_t k, int32_t* out_ids_dev,
+                         void* out_dist_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------ testing */
+
+/*
+ * hc_debug_fail_alloc -- host-side fault injection (no counterpart in the
+ * paper; it exists so that allocation-failure handling can be tested without
+ * exhausting a GPU).  After this call, the library allocation numbered
+ * `after` (0-based, counting device allocations made by any entry point)
+ * fails as if the device were out of memory, and the entry point returns
+ * HC_ERR_OOM after releasing what it had allocated.  after < 0 disables the
+ * injection.  Not thread-safe with concurrent library calls.
+ */
+HC_API void hc_debug_fail_alloc(long after);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HC_H */

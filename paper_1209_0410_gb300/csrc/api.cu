@@ -1,0 +1,469 @@
+// The C ABI of include/hc.h: argument checks, ownership and allocation
+// around the kernels of keys.cu (K1), sort.cu (K2) and query.cu (K3..K6).
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hc_internal.h"
+
+using namespace hc;
+
+struct hc_index {
+    hc_build_params params{};
+    std::vector<uint32_t> dim_map;   // host copy, empty = consecutive
+    uint32_t* dim_map_dev = nullptr;
+    const void* db = nullptr;
+    void* db_owned = nullptr;
+    uint64_t* keys_hi = nullptr;
+    uint64_t* keys_lo = nullptr;
+    uint32_t* ids = nullptr;
+    uint64_t* list_off_dev = nullptr;
+    std::vector<uint64_t> list_off;
+    uint32_t lists = 0, row_bytes = 0;
+    // device staging of hc_query_host
+    void* st_q = nullptr;
+    void* st_out = nullptr;
+    size_t st_q_cap = 0, st_out_cap = 0;
+};
+
+namespace {
+
+// Host-side fault injection for tests: the allocation numbered fail_after
+// (0-based, counted from the hc_debug_fail_alloc call) reports OOM.
+std::atomic<long> g_fail_after{-1};
+std::atomic<long> g_alloc_count{0};
+
+bool injected_failure() {
+    const long after = g_fail_after.load();
+    if (after < 0) return false;
+    return g_alloc_count.fetch_add(1) == after;
+}
+
+int status_of(cudaError_t e) {
+    if (e == cudaSuccess) return HC_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return HC_ERR_OOM;
+    }
+    return HC_ERR_CUDA;
+}
+
+int dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (injected_failure()) return HC_ERR_OOM;
+    if (bytes == 0) bytes = 16;
+    return status_of(cudaMalloc(p, bytes));
+}
+
+int dev_alloc_async(void** p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (injected_failure()) return HC_ERR_OOM;
+    if (bytes == 0) bytes = 16;
+    return status_of(cudaMallocAsync(p, bytes, s));
+}
+
+void keep_pool_memory() {
+    // stream-ordered scratch is returned to the pool, not to the driver,
+    // between builds of this process
+    static std::atomic<bool> done{false};
+    if (done.exchange(true)) return;
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// true when p is device memory of the current device (or managed)
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+uint32_t row_bytes_of(hc_dtype t, uint32_t d) { return t == HC_F32 ? d * 4u : d; }
+
+int check_params(const hc_build_params* p) {
+    if (!p) return HC_ERR_ARG;
+    if (p->dtype != HC_U8 && p->dtype != HC_F32) return HC_ERR_ARG;
+    if (p->n < 1 || p->n >= (1ull << 31)) return HC_ERR_ARG;
+    if (p->d < 1 || p->d > 4096) return HC_ERR_ARG;
+    if (row_bytes_of(p->dtype, p->d) % 16 != 0) return HC_ERR_ARG;
+    if (p->curves < 1 || p->curves > 32) return HC_ERR_ARG;
+    if (p->dims_per_curve < 1 || p->dims_per_curve > 16) return HC_ERR_ARG;
+    if (p->bits != 8) return HC_ERR_ARG;
+    const uint32_t parts = p->partitions ? p->partitions : 1;
+    if ((uint64_t)parts * p->curves > 256) return HC_ERR_ARG;
+    if ((uint64_t)p->curves * p->n >= (1ull << 32)) return HC_ERR_ARG;
+    if (p->dim_map) {
+        for (uint32_t i = 0; i < p->curves * p->dims_per_curve; ++i)
+            if (p->dim_map[i] >= p->d) return HC_ERR_ARG;
+    } else if ((uint64_t)p->curves * p->dims_per_curve > p->d) {
+        return HC_ERR_ARG;
+    }
+    return HC_OK;
+}
+
+IndexView view_of(const hc_index* x) {
+    IndexView v;
+    v.db = x->db;
+    v.row_bytes = x->row_bytes;
+    v.d = x->params.d;
+    v.P = Projection{x->params.d, x->params.curves, x->params.dims_per_curve, x->dim_map_dev,
+                     x->params.dtype};
+    v.lists = x->lists;
+    v.list_off = x->list_off_dev;
+    v.keys_hi = x->keys_hi;
+    v.keys_lo = x->keys_lo;
+    v.ids = x->ids;
+    return v;
+}
+
+void destroy(hc_index* x) {
+    if (!x) return;
+    cudaFree(x->dim_map_dev);
+    cudaFree(x->db_owned);
+    cudaFree(x->keys_hi);
+    cudaFree(x->keys_lo);
+    cudaFree(x->ids);
+    cudaFree(x->list_off_dev);
+    cudaFree(x->st_q);
+    cudaFree(x->st_out);
+    cudaGetLastError();
+    delete x;
+}
+
+// Algorithm 1 for an index whose params, db and dim_map are set.
+int build_index(hc_index* x, cudaStream_t s) {
+    const hc_build_params& P = x->params;
+    const uint32_t parts = P.partitions;
+    x->lists = parts * P.curves;
+    x->row_bytes = row_bytes_of(P.dtype, P.d);
+    x->list_off.assign(x->lists + 1, 0);
+    for (uint32_t L = 0; L < x->lists; ++L) {
+        const uint32_t j = L / P.curves;
+        const uint64_t len = partition_start(j + 1, P.n, parts) - partition_start(j, P.n, parts);
+        x->list_off[L + 1] = x->list_off[L] + len;
+    }
+    const uint64_t total = x->list_off[x->lists];
+    int rc;
+    if ((rc = dev_alloc((void**)&x->list_off_dev, sizeof(uint64_t) * (x->lists + 1)))) return rc;
+    if (!x->dim_map.empty()) {
+        if ((rc = dev_alloc((void**)&x->dim_map_dev, sizeof(uint32_t) * x->dim_map.size())))
+            return rc;
+        if ((rc = status_of(cudaMemcpyAsync(x->dim_map_dev, x->dim_map.data(),
+                                            sizeof(uint32_t) * x->dim_map.size(),
+                                            cudaMemcpyHostToDevice, s))))
+            return rc;
+    }
+    if ((rc = status_of(cudaMemcpyAsync(x->list_off_dev, x->list_off.data(),
+                                        sizeof(uint64_t) * (x->lists + 1), cudaMemcpyHostToDevice,
+                                        s))))
+        return rc;
+    if ((rc = dev_alloc((void**)&x->keys_hi, sizeof(uint64_t) * total))) return rc;
+    if ((rc = dev_alloc((void**)&x->keys_lo, sizeof(uint64_t) * total))) return rc;
+    if ((rc = dev_alloc((void**)&x->ids, sizeof(uint32_t) * total))) return rc;
+
+    SortProblem sp;
+    sp.seg_off = x->list_off;
+    sp.key_bits = 8 * P.dims_per_curve;
+    sp.out_hi = x->keys_hi;
+    sp.out_lo = x->keys_lo;
+    sp.out_ids = x->ids;
+    const size_t sort_bytes = sort_scratch_bytes(sp);
+    const size_t key_bytes = (sizeof(uint64_t) * 2 + sizeof(uint32_t)) * total;
+    keep_pool_memory();
+    void* scratch = nullptr;
+    if ((rc = dev_alloc_async(&scratch, key_bytes + 256 + sort_bytes, s))) return rc;
+    uint64_t* hi0 = static_cast<uint64_t*>(scratch);
+    uint64_t* lo0 = hi0 + total;
+    uint32_t* ids0 = reinterpret_cast<uint32_t*>(lo0 + total);
+    void* sort_scratch = static_cast<char*>(scratch) + ((key_bytes + 255) & ~(size_t)255);
+
+    BuildKeysArgs ka{x->db, P.n, x->row_bytes, view_of(x).P, parts, x->list_off_dev, hi0, lo0,
+                     ids0};
+    rc = status_of(launch_build_keys(ka, s));
+    if (rc == HC_OK) {
+        sp.hi = hi0;
+        sp.lo = lo0;
+        sp.ids = ids0;
+        rc = sort_segments(sp, sort_scratch, s);
+    }
+    const int frc = status_of(cudaFreeAsync(scratch, s));
+    return rc ? rc : frc;
+}
+
+int new_index(const void* db, const hc_build_params* params, hc_index** out, hc_index** made) {
+    *made = nullptr;
+    if (!out) return HC_ERR_ARG;
+    *out = nullptr;
+    if (int rc = check_params(params)) return rc;
+    hc_index* x = new (std::nothrow) hc_index();
+    if (!x) return HC_ERR_OOM;
+    x->params = *params;
+    if (!x->params.partitions) x->params.partitions = 1;
+    if (params->dim_map)
+        x->dim_map.assign(params->dim_map, params->dim_map + params->curves * params->dims_per_curve);
+    x->params.dim_map = nullptr;
+    x->db = db;
+    *made = x;
+    return HC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+HC_API const char* hc_strerror(int status) {
+    switch (status) {
+        case HC_OK: return "ok";
+        case HC_PENDING: return "pending";
+        case HC_ERR_ARG: return "invalid argument";
+        case HC_ERR_OOM: return "out of memory";
+        case HC_ERR_CUDA: return "CUDA runtime error";
+        case HC_ERR_BUDGET: return "admission refused: over the memory budget";
+        case HC_ERR_TIMEOUT: return "timed out";
+        case HC_ERR_DEVICE_STATUS: return "a kernel reported an error status";
+        case HC_ERR_STATE: return "object in the wrong state";
+        default: return "unknown status";
+    }
+}
+
+HC_API int hc_build(const void* db_dev, const hc_build_params* params, void* cuda_stream,
+                    hc_index** out) {
+    hc_index* x;
+    if (int rc = new_index(db_dev, params, out, &x)) return rc;
+    if (!is_device_ptr(db_dev) || !aligned16(db_dev)) {
+        destroy(x);
+        return HC_ERR_ARG;
+    }
+    const int rc = build_index(x, static_cast<cudaStream_t>(cuda_stream));
+    if (rc) {
+        cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+        destroy(x);
+        return rc;
+    }
+    *out = x;
+    return HC_OK;
+}
+
+HC_API int hc_build_host(const void* db_host, const hc_build_params* params, void* cuda_stream,
+                         hc_index** out) {
+    if (!db_host) return HC_ERR_ARG;
+    hc_index* x;
+    if (int rc = new_index(nullptr, params, out, &x)) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t bytes = (size_t)params->n * row_bytes_of(params->dtype, params->d);
+    int rc = dev_alloc(&x->db_owned, bytes);
+    if (!rc) rc = status_of(cudaMemcpyAsync(x->db_owned, db_host, bytes, cudaMemcpyHostToDevice, s));
+    x->db = x->db_owned;
+    if (!rc) rc = build_index(x, s);
+    const int src = status_of(cudaStreamSynchronize(s));
+    if (!rc) rc = src;
+    if (rc) {
+        destroy(x);
+        return rc;
+    }
+    *out = x;
+    return HC_OK;
+}
+
+HC_API void hc_free(hc_index* idx) { destroy(idx); }
+
+HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
+                    int32_t* out_ids_dev, void* out_dist_dev, void* cuda_stream) {
+    if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
+    if (nq == 0) return HC_OK;
+    if (!q_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev)) return HC_ERR_ARG;
+    if (!is_device_ptr(q_dev) || !is_device_ptr(out_ids_dev) || !is_device_ptr(out_dist_dev))
+        return HC_ERR_ARG;
+    return status_of(launch_query(view_of(idx), q_dev, nq, k, p, out_ids_dev, out_dist_dev,
+                                  static_cast<cudaStream_t>(cuda_stream)));
+}
+
+HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,
+                         int32_t* out_ids_host, void* out_dist_host, void* cuda_stream) {
+    if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
+    if (nq == 0) return HC_OK;
+    if (!q_host || !out_ids_host || !out_dist_host) return HC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t qbytes = (size_t)nq * idx->row_bytes;
+    const size_t obytes = (size_t)nq * k * 4;
+    int rc;
+    if (qbytes > idx->st_q_cap) {
+        cudaStreamSynchronize(s);
+        cudaFree(idx->st_q);
+        idx->st_q_cap = 0;
+        if ((rc = dev_alloc(&idx->st_q, qbytes))) return rc;
+        idx->st_q_cap = qbytes;
+    }
+    if (2 * obytes > idx->st_out_cap) {
+        cudaStreamSynchronize(s);
+        cudaFree(idx->st_out);
+        idx->st_out_cap = 0;
+        if ((rc = dev_alloc(&idx->st_out, 2 * obytes))) return rc;
+        idx->st_out_cap = 2 * obytes;
+    }
+    int32_t* d_ids = static_cast<int32_t*>(idx->st_out);
+    void* d_dist = static_cast<char*>(idx->st_out) + obytes;
+    if ((rc = status_of(cudaMemcpyAsync(idx->st_q, q_host, qbytes, cudaMemcpyHostToDevice, s))))
+        return rc;
+    if ((rc = status_of(launch_query(view_of(idx), idx->st_q, nq, k, p, d_ids, d_dist, s))))
+        return rc;
+    if ((rc = status_of(cudaMemcpyAsync(out_ids_host, d_ids, obytes, cudaMemcpyDeviceToHost, s))))
+        return rc;
+    if ((rc = status_of(cudaMemcpyAsync(out_dist_host, d_dist, obytes, cudaMemcpyDeviceToHost, s))))
+        return rc;
+    return status_of(cudaStreamSynchronize(s));
+}
+
+HC_API int hc_index_describe(const hc_index* idx, hc_index_info* info, uint64_t* list_off_host) {
+    if (!idx || !info) return HC_ERR_ARG;
+    info->n = idx->params.n;
+    info->d = idx->params.d;
+    info->curves = idx->params.curves;
+    info->dims_per_curve = idx->params.dims_per_curve;
+    info->partitions = idx->params.partitions;
+    info->lists = idx->lists;
+    info->dtype = idx->params.dtype;
+    info->keys_hi_dev = idx->keys_hi;
+    info->keys_lo_dev = idx->keys_lo;
+    info->ids_dev = idx->ids;
+    info->db_dev = idx->db;
+    if (list_off_host)
+        std::memcpy(list_off_host, idx->list_off.data(), sizeof(uint64_t) * (idx->lists + 1));
+    return HC_OK;
+}
+
+HC_API int hc_index_copy_lists(const hc_index* idx, uint64_t* keys_hi_dev, uint64_t* keys_lo_dev,
+                               uint32_t* ids_dev, void* cuda_stream) {
+    if (!idx) return HC_ERR_ARG;
+    const uint64_t total = idx->list_off[idx->lists];
+    if (total == 0) return HC_OK;
+    if (!is_device_ptr(keys_hi_dev) || !is_device_ptr(keys_lo_dev) || !is_device_ptr(ids_dev))
+        return HC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int rc = status_of(cudaMemcpyAsync(keys_hi_dev, idx->keys_hi, 8 * total,
+                                       cudaMemcpyDeviceToDevice, s));
+    if (!rc)
+        rc = status_of(cudaMemcpyAsync(keys_lo_dev, idx->keys_lo, 8 * total,
+                                       cudaMemcpyDeviceToDevice, s));
+    if (!rc)
+        rc = status_of(cudaMemcpyAsync(ids_dev, idx->ids, 4 * total, cudaMemcpyDeviceToDevice, s));
+    return rc;
+}
+
+HC_API int hc_hilbert_keys(const void* x_dev, hc_dtype dtype, uint64_t count, uint32_t d,
+                           uint32_t curves, uint32_t m, const uint32_t* dim_map_host,
+                           uint64_t* hi_dev, uint64_t* lo_dev, void* cuda_stream) {
+    if (dtype != HC_U8 && dtype != HC_F32) return HC_ERR_ARG;
+    if (d < 1 || d > 4096 || curves < 1 || curves > 32 || m < 1 || m > 16) return HC_ERR_ARG;
+    const uint32_t rb = row_bytes_of(dtype, d);
+    if (rb % 16) return HC_ERR_ARG;
+    if (dim_map_host) {
+        for (uint32_t i = 0; i < curves * m; ++i)
+            if (dim_map_host[i] >= d) return HC_ERR_ARG;
+    } else if ((uint64_t)curves * m > d) {
+        return HC_ERR_ARG;
+    }
+    if (count == 0) return HC_OK;
+    if (!is_device_ptr(x_dev) || !aligned16(x_dev) || !is_device_ptr(hi_dev) ||
+        !is_device_ptr(lo_dev))
+        return HC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    uint32_t* dm = nullptr;
+    int rc;
+    if (dim_map_host) {
+        if ((rc = dev_alloc_async((void**)&dm, sizeof(uint32_t) * curves * m, s))) return rc;
+        if ((rc = status_of(cudaMemcpyAsync(dm, dim_map_host, sizeof(uint32_t) * curves * m,
+                                            cudaMemcpyHostToDevice, s)))) {
+            cudaFreeAsync(dm, s);
+            return rc;
+        }
+    }
+    Projection P{d, curves, m, dm, dtype};
+    rc = status_of(launch_vector_keys(x_dev, count, rb, P, hi_dev, lo_dev, s));
+    if (dm) {
+        // the copy above reads a host buffer the caller may free after return
+        cudaStreamSynchronize(s);
+        cudaFreeAsync(dm, s);
+    }
+    return rc;
+}
+
+HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
+                        const uint64_t* seg_off_host, uint32_t nseg, uint32_t key_bits,
+                        void* cuda_stream) {
+    if (!seg_off_host || nseg < 1 || key_bits < 1 || key_bits > 128) return HC_ERR_ARG;
+    for (uint32_t i = 0; i < nseg; ++i)
+        if (seg_off_host[i + 1] < seg_off_host[i]) return HC_ERR_ARG;
+    if (seg_off_host[0] != 0) return HC_ERR_ARG;
+    const uint64_t total = seg_off_host[nseg];
+    if (total >= (1ull << 32)) return HC_ERR_ARG;
+    if (total == 0) return HC_OK;
+    if (!is_device_ptr(hi_dev) || !is_device_ptr(lo_dev) || !is_device_ptr(ids_dev))
+        return HC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    SortProblem sp;
+    sp.hi = hi_dev;
+    sp.lo = lo_dev;
+    sp.ids = ids_dev;
+    sp.seg_off.assign(seg_off_host, seg_off_host + nseg + 1);
+    sp.key_bits = key_bits;
+    const size_t out_bytes = (sizeof(uint64_t) * 2 + sizeof(uint32_t)) * total;
+    const size_t sb = sort_scratch_bytes(sp);
+    keep_pool_memory();
+    void* buf = nullptr;
+    int rc;
+    if ((rc = dev_alloc_async(&buf, out_bytes + 256 + sb, s))) return rc;
+    sp.out_hi = static_cast<uint64_t*>(buf);
+    sp.out_lo = sp.out_hi + total;
+    sp.out_ids = reinterpret_cast<uint32_t*>(sp.out_lo + total);
+    rc = sort_segments(sp, static_cast<char*>(buf) + ((out_bytes + 255) & ~(size_t)255), s);
+    if (!rc) rc = status_of(cudaMemcpyAsync(hi_dev, sp.out_hi, 8 * total, cudaMemcpyDeviceToDevice, s));
+    if (!rc) rc = status_of(cudaMemcpyAsync(lo_dev, sp.out_lo, 8 * total, cudaMemcpyDeviceToDevice, s));
+    if (!rc)
+        rc = status_of(cudaMemcpyAsync(ids_dev, sp.out_ids, 4 * total, cudaMemcpyDeviceToDevice, s));
+    const int frc = status_of(cudaFreeAsync(buf, s));
+    const int src = status_of(cudaStreamSynchronize(s));
+    return rc ? rc : (frc ? frc : src);
+}
+
+HC_API int hc_query_positions(hc_index* idx, const void* q_dev, uint32_t nq, int64_t* pos_dev,
+                              void* cuda_stream) {
+    if (!idx) return HC_ERR_ARG;
+    if (nq == 0) return HC_OK;
+    if (!is_device_ptr(q_dev) || !aligned16(q_dev) || !is_device_ptr(pos_dev)) return HC_ERR_ARG;
+    return status_of(
+        launch_positions(view_of(idx), q_dev, nq, pos_dev, static_cast<cudaStream_t>(cuda_stream)));
+}
+
+HC_API int hc_bruteforce(const void* db_dev, hc_dtype dtype, uint64_t n, uint32_t d,
+                         const void* q_dev, uint32_t nq, uint32_t k, int32_t* out_ids_dev,
+                         void* out_dist_dev, void* cuda_stream) {
+    if (dtype != HC_U8 && dtype != HC_F32) return HC_ERR_ARG;
+    if (k < 1 || k > 128 || d < 1 || d > 4096 || n >= (1ull << 31)) return HC_ERR_ARG;
+    if (row_bytes_of(dtype, d) % 16) return HC_ERR_ARG;
+    if (nq == 0) return HC_OK;
+    if (!is_device_ptr(db_dev) || !is_device_ptr(q_dev) || !is_device_ptr(out_ids_dev) ||
+        !is_device_ptr(out_dist_dev) || !aligned16(db_dev) || !aligned16(q_dev))
+        return HC_ERR_ARG;
+    return status_of(launch_bruteforce(db_dev, dtype, n, d, q_dev, nq, k, out_ids_dev, out_dist_dev,
+                                       static_cast<cudaStream_t>(cuda_stream)));
+}
+
+HC_API void hc_debug_fail_alloc(long after) {
+    g_alloc_count.store(0);
+    g_fail_after.store(after);
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// Host-side declarations shared by the libhc translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "hc.h"
+#include "hc_device.cuh"
+
+namespace hc {
+
+// ------------------------------------------------------------ K1: keys
+// Keys of every row for every curve, written at the row's slot of each list
+// of its partition: list L = part*curves + c, slot list_off[L] + (r - start).
+struct BuildKeysArgs {
+    const void* db;
+    uint64_t n;
+    uint32_t row_bytes;
+    Projection P;
+    uint32_t partitions;
+    const uint64_t* list_off;  // device, lists+1
+    uint64_t* hi;
+    uint64_t* lo;
+    uint32_t* ids;
+};
+cudaError_t launch_build_keys(const BuildKeysArgs& a, cudaStream_t s);
+
+// count x curves keys of standalone vectors
+cudaError_t launch_vector_keys(const void* x, uint64_t count, uint32_t row_bytes,
+                               const Projection& P, uint64_t* hi, uint64_t* lo, cudaStream_t s);
+
+// ------------------------------------------------------------ K2: sort
+// Stable LSD radix sort of 128-bit keys by segment.  The sources stay
+// untouched; the sorted keys and the carried ids land in out_*.
+struct SortProblem {
+    const uint64_t* hi;        // device, total records
+    const uint64_t* lo;
+    const uint32_t* ids;
+    std::vector<uint64_t> seg_off;  // host, nseg+1
+    uint32_t key_bits;         // 1..128
+    uint64_t* out_hi;          // device, total records (distinct from sources)
+    uint64_t* out_lo;
+    uint32_t* out_ids;
+};
+// Scratch bytes the sort needs for this problem (queried before allocating).
+size_t sort_scratch_bytes(const SortProblem& p);
+// Enqueues the whole sort on s using the given scratch (>= sort_scratch_bytes).
+int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s);
+
+// ---------------------------------------------------- K3..K6: queries
+struct IndexView {
+    const void* db;
+    uint32_t row_bytes;
+    uint32_t d;
+    Projection P;
+    uint32_t lists;            // partitions * curves
+    const uint64_t* list_off;  // device, lists+1
+    const uint64_t* keys_hi;
+    const uint64_t* keys_lo;
+    const uint32_t* ids;
+};
+
+cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
+                         int32_t* out_ids, void* out_dist, cudaStream_t s);
+cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, int64_t* pos,
+                             cudaStream_t s);
+cudaError_t launch_bruteforce(const void* db, hc_dtype dtype, uint64_t n, uint32_t d,
+                              const void* q, uint32_t nq, uint32_t k, int32_t* out_ids,
+                              void* out_dist, cudaStream_t s);
+
+}  // namespace hc

@@ -1,0 +1,65 @@
+// K1: Hilbert extended-keys of database rows (Algorithm 1, per-curve step)
+// and of standalone vectors.  One thread per row computes the keys of every
+// curve; the Hilbert map itself is ALU work (about 800 integer operations
+// per 16-coordinate key), the row read and the 20 bytes written per key are
+// coalesced across the warp.
+#include "hc_internal.h"
+
+namespace hc {
+
+__global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += stride) {
+        const uint32_t part = partition_of(r, a.n, a.partitions);
+        const uint64_t local = r - partition_start(part, a.n, a.partitions);
+        const void* row = static_cast<const uint8_t*>(a.db) + r * a.row_bytes;
+        for (uint32_t c = 0; c < a.P.curves; ++c) {
+            uint64_t hi, lo;
+            curve_key(row, a.P, c, hi, lo);
+            const uint64_t g = a.list_off[part * a.P.curves + c] + local;
+            a.hi[g] = hi;
+            a.lo[g] = lo;
+            a.ids[g] = (uint32_t)r;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) vector_keys_kernel(const void* x, uint64_t count,
+                                                          uint32_t row_bytes, Projection P,
+                                                          uint64_t* hi, uint64_t* lo) {
+    const uint64_t total = count * P.curves;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const uint64_t v = t / P.curves;
+        const uint32_t c = (uint32_t)(t % P.curves);
+        uint64_t h, l;
+        curve_key(static_cast<const uint8_t*>(x) + v * row_bytes, P, c, h, l);
+        hi[t] = h;
+        lo[t] = l;
+    }
+}
+
+static unsigned grid_for(uint64_t work, unsigned threads) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (work + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)sms * 16;   // grid-stride beyond 16 waves of 256
+    return (unsigned)(want < cap ? (want ? want : 1) : cap);
+}
+
+cudaError_t launch_build_keys(const BuildKeysArgs& a, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    build_keys_kernel<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vector_keys(const void* x, uint64_t count, uint32_t row_bytes,
+                               const Projection& P, uint64_t* hi, uint64_t* lo, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    vector_keys_kernel<<<grid_for(count * P.curves, 256), 256, 0, s>>>(x, count, row_bytes, P, hi,
+                                                                       lo);
+    return cudaGetLastError();
+}
+
+}  // namespace hc

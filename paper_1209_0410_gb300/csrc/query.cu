@@ -1,0 +1,324 @@
+// K3..K6: the fused query kernel (Algorithm 2 for a batch of queries) and the
+// exact brute-force kNN (Eq. 3) that shares its distance and top-k code.
+//
+// One warp per query:
+//   K1  lanes c < curves compute the query's extended-key on curve c;
+//   K3  lanes L < lists run lower_bound in list L (128-bit compares, the low
+//       word is read only when the high words tie);
+//   K4  for every list, the window [max(0,pos-p), min(n,pos+p)) is walked 32
+//       entries at a time: the 32 ids are one coalesced load, then each row
+//       is read as 16-byte vectors by LPR lanes (LPR = 8 for 128-byte uint8
+//       rows: four rows per warp instruction, up to eight instructions in
+//       flight per lane); uint8 partial distances use vabsdiffu4 + dp4a
+//       (exact in 32-bit integers), float32 use fma;
+//       a reduce-scatter over the LPR lanes leaves lane l with the distance
+//       of one row of the 32 (LPR-1 shuffles for LPR partial sums);
+//   K5/K6 the 32 packed (distance, id) candidates are offered to one running
+//       warp top-k for the whole query, which drops duplicate ids: the union
+//       over curves and partitions and the Aggregator's reduction in one.
+// The path is a gather bounded by HBM bandwidth; no tensor cores are used.
+#include <algorithm>
+
+#include "hc_internal.h"
+#include "hc_topk.cuh"
+
+namespace hc {
+
+namespace {
+
+constexpr int kQWarps = 8;
+
+struct QueryArgs {
+    IndexView ix;
+    const void* q;
+    uint32_t nq, k, p;
+    int32_t* out_ids;
+    void* out_dist;
+    int64_t* out_pos;   // positions-only kernel
+};
+
+__device__ __forceinline__ uint4 ldg16(const void* p) {
+    return __ldg(reinterpret_cast<const uint4*>(p));
+}
+
+__device__ __forceinline__ uint32_t acc_vec(uint4 a, uint4 b, uint32_t acc) {
+    uint32_t t;
+    t = __vabsdiffu4(a.x, b.x);
+    acc = __dp4a(t, t, acc);
+    t = __vabsdiffu4(a.y, b.y);
+    acc = __dp4a(t, t, acc);
+    t = __vabsdiffu4(a.z, b.z);
+    acc = __dp4a(t, t, acc);
+    t = __vabsdiffu4(a.w, b.w);
+    acc = __dp4a(t, t, acc);
+    return acc;
+}
+
+__device__ __forceinline__ float acc_vec(uint4 a, uint4 b, float acc) {
+    float t;
+    t = __uint_as_float(a.x) - __uint_as_float(b.x);
+    acc = fmaf(t, t, acc);
+    t = __uint_as_float(a.y) - __uint_as_float(b.y);
+    acc = fmaf(t, t, acc);
+    t = __uint_as_float(a.z) - __uint_as_float(b.z);
+    acc = fmaf(t, t, acc);
+    t = __uint_as_float(a.w) - __uint_as_float(b.w);
+    acc = fmaf(t, t, acc);
+    return acc;
+}
+
+__device__ __forceinline__ uint32_t dist_bits(uint32_t d) { return d; }
+__device__ __forceinline__ uint32_t dist_bits(float d) { return __float_as_uint(d); }
+
+// v[j] = this lane's partial of sub-batch j (j < LPR).  Returns the full sum of
+// sub-batch (lane % LPR) over the LPR lanes of the lane's group.
+template <int LPR, typename Acc>
+__device__ __forceinline__ Acc reduce_scatter(Acc (&v)[LPR], uint32_t s) {
+#pragma unroll
+    for (int w = LPR / 2; w >= 1; w >>= 1) {
+        const bool upper = (s & (uint32_t)w) != 0;
+#pragma unroll
+        for (int t = 0; t < w; ++t) {
+            const Acc send = upper ? v[t] : v[t + w];
+            const Acc keep = upper ? v[t + w] : v[t];
+            v[t] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0];
+}
+
+// Distances of up to 32 rows (row r of the chunk has id shfl(id, r), valid
+// for r < cnt) to the query; returns this lane's packed candidate: the row
+// (lane % LPR) * (32 / LPR) + lane / LPR of the chunk, or kEmpty.
+template <bool F32, int LPR>
+__device__ __forceinline__ uint64_t chunk_candidates(const uint8_t* __restrict__ db,
+                                                     uint32_t row_bytes, const uint8_t* qrow,
+                                                     uint4 qv0, uint32_t id, uint32_t cnt,
+                                                     int lane) {
+    using Acc = typename std::conditional<F32, float, uint32_t>::type;
+    constexpr int RPI = 32 / LPR;
+    constexpr int G = LPR < 8 ? LPR : 8;
+    const uint32_t s = (uint32_t)lane % LPR, g = (uint32_t)lane / LPR;
+    const uint32_t vecs = row_bytes >> 4;
+    const uint32_t vpl = (vecs + LPR - 1) / LPR;
+    Acc part[LPR];
+#pragma unroll
+    for (int j = 0; j < LPR; ++j) part[j] = Acc(0);
+    for (uint32_t v = 0; v < vpl; ++v) {
+        const uint32_t col = s + v * LPR;
+        const bool colok = col < vecs;
+        const uint4 qv = v == 0 ? qv0 : (colok ? ldg16(qrow + col * 16) : make_uint4(0, 0, 0, 0));
+#pragma unroll
+        for (int j0 = 0; j0 < LPR; j0 += G) {
+            uint4 rv[G];
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const uint32_t r = (uint32_t)(j0 + j) * RPI + g;
+                const uint32_t rid = __shfl_sync(0xffffffffu, id, (int)r);
+                rv[j] = (r < cnt && colok) ? ldg16(db + (size_t)rid * row_bytes + col * 16)
+                                           : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int j = 0; j < G; ++j) part[j0 + j] = acc_vec(rv[j], qv, part[j0 + j]);
+        }
+    }
+    const Acc dsum = reduce_scatter<LPR>(part, s);
+    const uint32_t r = s * RPI + g;
+    const uint32_t cid = __shfl_sync(0xffffffffu, id, (int)r);
+    return r < cnt ? ((uint64_t)dist_bits(dsum) << 32) | cid : kEmpty;
+}
+
+// first i in [0, n) with key[i] >= (kh, kl), else n
+__device__ __forceinline__ uint32_t lower_bound_key(const uint64_t* __restrict__ hi,
+                                                    const uint64_t* __restrict__ lo, uint32_t n,
+                                                    uint64_t kh, uint64_t kl) {
+    uint32_t first = 0, count = n;
+    while (count > 0) {
+        const uint32_t step = count >> 1, mid = first + step;
+        const uint64_t h = __ldg(hi + mid);
+        bool less = h < kh;
+        if (h == kh) less = __ldg(lo + mid) < kl;
+        if (less) {
+            first = mid + 1;
+            count -= step + 1;
+        } else {
+            count = step;
+        }
+    }
+    return first;
+}
+
+// K1 + K3 for one query: positions of the query key in every list, written
+// to pos_w[0..lists).
+__device__ __forceinline__ void query_positions(const IndexView& ix, const uint8_t* qrow,
+                                                uint32_t* pos_w, int lane) {
+    const uint32_t curves = ix.P.curves;
+    uint64_t khi = 0, klo = 0;
+    if ((uint32_t)lane < curves) curve_key(qrow, ix.P, (uint32_t)lane, khi, klo);
+    for (uint32_t b = 0; b < ix.lists; b += 32) {
+        const uint32_t L = b + (uint32_t)lane;
+        const int c = (int)(L % curves);
+        const uint64_t kh = __shfl_sync(0xffffffffu, khi, c);
+        const uint64_t kl = __shfl_sync(0xffffffffu, klo, c);
+        if (L < ix.lists) {
+            const uint64_t off = ix.list_off[L];
+            const uint32_t n = (uint32_t)(ix.list_off[L + 1] - off);
+            pos_w[L] = lower_bound_key(ix.keys_hi + off, ix.keys_lo + off, n, kh, kl);
+        }
+    }
+    __syncwarp();
+}
+
+template <bool F32, int LPR, int KR>
+__global__ void __launch_bounds__(kQWarps * 32) query_kernel(QueryArgs a) {
+    extern __shared__ uint32_t s_pos[];  // kQWarps x lists
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t qi = blockIdx.x * kQWarps + warp;
+    if (qi >= a.nq) return;
+    const IndexView& ix = a.ix;
+    const uint8_t* qrow = static_cast<const uint8_t*>(a.q) + (size_t)qi * ix.row_bytes;
+    uint32_t* pos_w = s_pos + warp * ix.lists;
+    query_positions(ix, qrow, pos_w, lane);
+
+    const uint32_t s = (uint32_t)lane % LPR;
+    const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
+    const uint8_t* db = static_cast<const uint8_t*>(ix.db);
+
+    WarpTopK<KR> top;
+    top.init();
+    for (uint32_t L = 0; L < ix.lists; ++L) {
+        const uint64_t off = ix.list_off[L];
+        const uint32_t n = (uint32_t)(ix.list_off[L + 1] - off);
+        const uint32_t pos = pos_w[L];
+        const uint32_t lo = pos > a.p ? pos - a.p : 0u;
+        const uint32_t hi = (uint64_t)pos + a.p < (uint64_t)n ? pos + a.p : n;
+        const uint32_t* idl = ix.ids + off;
+        uint32_t next = lo + (uint32_t)lane < hi ? __ldg(idl + lo + lane) : 0u;
+        for (uint32_t base = lo; base < hi; base += 32) {
+            const uint32_t id = next;
+            const uint32_t cnt = min(32u, hi - base);
+            if (base + 32 < hi)
+                next = base + 32 + (uint32_t)lane < hi ? __ldg(idl + base + 32 + lane) : 0u;
+            const uint64_t cand =
+                chunk_candidates<F32, LPR>(db, ix.row_bytes, qrow, qv0, id, cnt, lane);
+            top.offer(cand, a.k, lane);
+        }
+    }
+    top.template store<F32>(a.k, lane, a.out_ids + (size_t)qi * a.k,
+                            static_cast<uint32_t*>(a.out_dist) + (size_t)qi * a.k);
+}
+
+__global__ void __launch_bounds__(kQWarps * 32) positions_kernel(QueryArgs a) {
+    extern __shared__ uint32_t s_pos[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t qi = blockIdx.x * kQWarps + warp;
+    if (qi >= a.nq) return;
+    const uint8_t* qrow = static_cast<const uint8_t*>(a.q) + (size_t)qi * a.ix.row_bytes;
+    uint32_t* pos_w = s_pos + warp * a.ix.lists;
+    query_positions(a.ix, qrow, pos_w, lane);
+    for (uint32_t L = lane; L < a.ix.lists; L += 32)
+        a.out_pos[(size_t)qi * a.ix.lists + L] = (int64_t)pos_w[L];
+}
+
+// Exact kNN: every row of the database, 32 rows per step, same distance and
+// top-k code as the query kernel.
+template <bool F32, int LPR, int KR>
+__global__ void __launch_bounds__(kQWarps * 32) brute_kernel(const uint8_t* __restrict__ db,
+                                                            uint64_t n, uint32_t row_bytes,
+                                                            const uint8_t* __restrict__ q,
+                                                            uint32_t nq, uint32_t k,
+                                                            int32_t* out_ids, void* out_dist) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t qi = blockIdx.x * kQWarps + warp;
+    if (qi >= nq) return;
+    const uint8_t* qrow = q + (size_t)qi * row_bytes;
+    const uint32_t s = (uint32_t)lane % LPR;
+    const uint4 qv0 = s < (row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
+    WarpTopK<KR> top;
+    top.init();
+    for (uint64_t base = 0; base < n; base += 32) {
+        const uint32_t cnt = n - base < 32 ? (uint32_t)(n - base) : 32u;
+        const uint32_t id = (uint32_t)(base + lane);
+        const uint64_t cand = chunk_candidates<F32, LPR>(db, row_bytes, qrow, qv0, id, cnt, lane);
+        top.offer(cand, k, lane);
+    }
+    top.template store<F32>(k, lane, out_ids + (size_t)qi * k,
+                            static_cast<uint32_t*>(out_dist) + (size_t)qi * k);
+}
+
+int lanes_per_row(uint32_t row_bytes) {
+    const uint32_t vecs = row_bytes / 16;
+    if (vecs <= 4) return 4;
+    if (vecs <= 8) return 8;
+    if (vecs <= 16) return 16;
+    return 32;
+}
+
+int regs_for_k(uint32_t k) { return k <= 32 ? 1 : (k <= 64 ? 2 : 4); }
+
+// dispatch on (dtype, lanes per row, top-k registers)
+template <template <bool, int, int> class Launch, typename... Args>
+cudaError_t dispatch(bool f32, int lpr, int kr, Args... args) {
+#define HC_CASE(F, L, K)                                   \
+    if (f32 == F && lpr == L && kr == K) return Launch<F, L, K>::run(args...);
+#define HC_CASES_L(F, L) HC_CASE(F, L, 1) HC_CASE(F, L, 2) HC_CASE(F, L, 4)
+#define HC_CASES_F(F) HC_CASES_L(F, 4) HC_CASES_L(F, 8) HC_CASES_L(F, 16) HC_CASES_L(F, 32)
+    HC_CASES_F(false)
+    HC_CASES_F(true)
+#undef HC_CASES_F
+#undef HC_CASES_L
+#undef HC_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <bool F32, int LPR, int KR>
+struct QueryLaunch {
+    static cudaError_t run(const QueryArgs& a, cudaStream_t s) {
+        const unsigned blocks = (a.nq + kQWarps - 1) / kQWarps;
+        const size_t smem = sizeof(uint32_t) * kQWarps * a.ix.lists;
+        query_kernel<F32, LPR, KR><<<blocks, kQWarps * 32, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
+template <bool F32, int LPR, int KR>
+struct BruteLaunch {
+    static cudaError_t run(const uint8_t* db, uint64_t n, uint32_t row_bytes, const uint8_t* q,
+                           uint32_t nq, uint32_t k, int32_t* ids, void* dist, cudaStream_t s) {
+        const unsigned blocks = (nq + kQWarps - 1) / kQWarps;
+        brute_kernel<F32, LPR, KR><<<blocks, kQWarps * 32, 0, s>>>(db, n, row_bytes, q, nq, k,
+                                                                   ids, dist);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace
+
+cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
+                         int32_t* out_ids, void* out_dist, cudaStream_t s) {
+    if (nq == 0) return cudaSuccess;
+    QueryArgs a{ix, q, nq, k, p, out_ids, out_dist, nullptr};
+    return dispatch<QueryLaunch>(ix.P.dtype == HC_F32, lanes_per_row(ix.row_bytes), regs_for_k(k),
+                                 a, s);
+}
+
+cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, int64_t* pos,
+                             cudaStream_t s) {
+    if (nq == 0) return cudaSuccess;
+    QueryArgs a{ix, q, nq, 1, 0, nullptr, nullptr, pos};
+    const unsigned blocks = (nq + kQWarps - 1) / kQWarps;
+    positions_kernel<<<blocks, kQWarps * 32, sizeof(uint32_t) * kQWarps * ix.lists, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bruteforce(const void* db, hc_dtype dtype, uint64_t n, uint32_t d,
+                              const void* q, uint32_t nq, uint32_t k, int32_t* out_ids,
+                              void* out_dist, cudaStream_t s) {
+    if (nq == 0) return cudaSuccess;
+    const uint32_t row_bytes = dtype == HC_F32 ? d * 4 : d;
+    return dispatch<BruteLaunch>(dtype == HC_F32, lanes_per_row(row_bytes), regs_for_k(k),
+                                 static_cast<const uint8_t*>(db), n, row_bytes,
+                                 static_cast<const uint8_t*>(q), nq, k, out_ids, out_dist, s);
+}
+
+}  // namespace hc

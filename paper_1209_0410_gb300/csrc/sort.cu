@@ -1,0 +1,364 @@
+// K2: stable LSD radix sort of (128-bit key, id) records within segments --
+// the "insert <key, b> into the sorted list" of Algorithm 1, done in bulk.
+//
+// Digits are 8 bits, least significant first (digit t covers key bits
+// 8t..8t+7).  Each pass moves only the 64-bit key word that holds the digit
+// plus a 32-bit record position (12 bytes), not the whole 20-byte record:
+//   - passes over the low word carry (lo, position);
+//   - the high words are then gathered by position and the passes over the
+//     high word carry (hi, position);
+//   - at the end the low words and ids are gathered by the final positions.
+// Digits above key_bits are zero by contract and are skipped.
+//
+// Per pass, three kernels, none of which waits on another block:
+//   hist    one 4096-record tile per block: digit counts -> counts[seg][digit][tile]
+//   scan    one block per (segment, digit): exclusive scan over the tiles
+//   scatter one tile per block: stable in-tile ranking with __match_any_sync
+//           per warp round, a shared-memory reorder by digit, then coalesced
+//           runs to global memory.
+#include <algorithm>
+
+#include "hc_internal.h"
+
+namespace hc {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kIpt = 16;                       // records per thread
+constexpr int kTile = kThreads * kIpt;         // 4096 records per tile
+constexpr int kWarpItems = kTile / kWarps;     // 512 consecutive records per warp
+
+struct SegInfo {
+    uint64_t start;     // first record
+    uint64_t len;       // records
+    uint64_t cnt_base;  // offset of the segment's counts block (256 x ntiles)
+    uint32_t ntiles;
+    uint32_t tile0;     // first global tile of the segment
+};
+
+__device__ __forceinline__ void tile_of(const uint32_t* tile_seg, const SegInfo* segs,
+                                        SegInfo& si, uint32_t& lt, uint64_t& start,
+                                        uint32_t& count) {
+    const uint32_t t = blockIdx.x;
+    si = segs[tile_seg[t]];
+    lt = t - si.tile0;
+    start = si.start + (uint64_t)lt * kTile;
+    const uint64_t left = si.len - (uint64_t)lt * kTile;
+    count = (uint32_t)(left < (uint64_t)kTile ? left : (uint64_t)kTile);
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kWarps ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < kWarps; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kWarps) warp_sums[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t before = warp ? warp_sums[warp - 1] : 0u;
+    __syncthreads();  // warp_sums may be reused by the caller
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kThreads) hist_kernel(const uint64_t* __restrict__ words,
+                                                        int shift,
+                                                        const uint32_t* __restrict__ tile_seg,
+                                                        const SegInfo* __restrict__ segs,
+                                                        uint32_t* __restrict__ counts) {
+    __shared__ uint32_t h[256];
+    SegInfo si;
+    uint32_t lt, count;
+    uint64_t start;
+    tile_of(tile_seg, segs, si, lt, start, count);
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t* w = words + start;
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < count; i += kThreads)
+        atomicAdd(&h[(uint32_t)(__ldg(w + i) >> shift) & 0xFFu], 1u);
+    __syncthreads();
+    counts[si.cnt_base + (uint64_t)threadIdx.x * si.ntiles + lt] = h[threadIdx.x];
+}
+
+// grid (256 digits, segments): exclusive scan of one digit row over the tiles
+__global__ void __launch_bounds__(kThreads) scan_kernel(const SegInfo* __restrict__ segs,
+                                                        uint32_t* __restrict__ counts,
+                                                        uint32_t* __restrict__ totals) {
+    __shared__ uint32_t warp_sums[kWarps];
+    const SegInfo si = segs[blockIdx.y];
+    const uint32_t digit = blockIdx.x;
+    uint32_t* row = counts + si.cnt_base + (uint64_t)digit * si.ntiles;
+    const uint32_t T = si.ntiles;
+    const uint32_t per = (T + kThreads - 1) / kThreads;
+    const uint32_t b = min(T, threadIdx.x * per), e = min(T, b + per);
+    uint32_t sum = 0;
+    for (uint32_t i = b; i < e; ++i) sum += row[i];
+    uint32_t run = block_exclusive_scan(sum, warp_sums);
+    if (threadIdx.x == kThreads - 1) totals[(uint64_t)blockIdx.y * 256 + digit] = run + sum;
+    for (uint32_t i = b; i < e; ++i) {
+        const uint32_t c = row[i];
+        row[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) scatter_kernel(
+    const uint64_t* __restrict__ wsrc, const uint32_t* __restrict__ psrc,
+    uint64_t* __restrict__ wdst, uint32_t* __restrict__ pdst, int shift,
+    const uint32_t* __restrict__ tile_seg, const SegInfo* __restrict__ segs,
+    const uint32_t* __restrict__ counts, const uint32_t* __restrict__ totals) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* sw = reinterpret_cast<uint64_t*>(smem);            // kTile words
+    uint32_t* sp = reinterpret_cast<uint32_t*>(sw + kTile);      // kTile positions
+    __shared__ uint32_t whist[kWarps][256];
+    __shared__ uint32_t dstart[256];
+    __shared__ uint64_t gbase[256];
+    __shared__ uint32_t warp_sums[kWarps];
+
+    SegInfo si;
+    uint32_t lt, count;
+    uint64_t start;
+    tile_of(tile_seg, segs, si, lt, start, count);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) whist[w][threadIdx.x] = 0;
+
+    uint64_t wv[kIpt];
+    uint32_t pv[kIpt];
+    uint32_t off[kIpt];
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t i = warp * kWarpItems + j * 32 + lane;
+        const bool valid = i < count;
+        wv[j] = valid ? __ldg(wsrc + start + i) : 0ull;
+        pv[j] = valid ? (psrc ? __ldg(psrc + start + i) : (uint32_t)(start + i)) : 0u;
+    }
+    __syncthreads();
+
+    // stable ranking inside the warp's 512 consecutive records, round by round
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t i = warp * kWarpItems + j * 32 + lane;
+        const bool valid = i < count;
+        const uint32_t dg = valid ? (uint32_t)(wv[j] >> shift) & 0xFFu : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t rank = __popc(peers & lanemask_lt);
+        const uint32_t base = valid ? whist[warp][dg] : 0u;
+        __syncwarp();
+        if (valid && rank == 0) whist[warp][dg] = base + __popc(peers);
+        __syncwarp();
+        off[j] = base + rank;
+    }
+    __syncthreads();
+
+    // per digit: offsets of each warp's run, the tile's digit starts, and the
+    // global base of the digit's run for this tile
+    {
+        const uint32_t dg = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = whist[w][dg];
+            whist[w][dg] = run;
+            run += c;
+        }
+        const uint32_t tile_start = block_exclusive_scan(run, warp_sums);
+        const uint32_t seg = __ldg(tile_seg + blockIdx.x);
+        const uint32_t seg_prefix =
+            block_exclusive_scan(__ldg(totals + (uint64_t)seg * 256 + dg), warp_sums);
+        dstart[dg] = tile_start;
+        const uint32_t before = __ldg(counts + si.cnt_base + (uint64_t)dg * si.ntiles + lt);
+        gbase[dg] = si.start + seg_prefix + before - tile_start;
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t i = warp * kWarpItems + j * 32 + lane;
+        if (i < count) {
+            const uint32_t dg = (uint32_t)(wv[j] >> shift) & 0xFFu;
+            const uint32_t pos = dstart[dg] + whist[warp][dg] + off[j];
+            sw[pos] = wv[j];
+            sp[pos] = pv[j];
+        }
+    }
+    __syncthreads();
+
+    for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
+        const uint64_t v = sw[i];
+        const uint64_t g = gbase[(uint32_t)(v >> shift) & 0xFFu] + i;
+        wdst[g] = v;
+        pdst[g] = sp[i];
+    }
+}
+
+// dst[i] = src[pos[i]] (pos == nullptr: identity)
+__global__ void __launch_bounds__(256) gather_words_kernel(const uint64_t* __restrict__ src,
+                                                           const uint32_t* __restrict__ pos,
+                                                           uint64_t* __restrict__ dst,
+                                                           uint64_t total) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
+        dst[i] = __ldg(src + (pos ? __ldg(pos + i) : i));
+}
+
+__global__ void __launch_bounds__(256) gather_final_kernel(
+    const uint64_t* __restrict__ lo, const uint32_t* __restrict__ ids,
+    const uint32_t* __restrict__ pos, uint64_t* __restrict__ out_lo,
+    uint32_t* __restrict__ out_ids, uint64_t total) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const uint32_t p = pos ? __ldg(pos + i) : (uint32_t)i;
+        out_lo[i] = __ldg(lo + p);
+        out_ids[i] = __ldg(ids + p);
+    }
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    uint64_t total = 0;
+    uint32_t nseg = 0, ntiles = 0;
+    uint64_t ncounts = 0;
+    std::vector<SegInfo> segs;
+    std::vector<uint32_t> tile_seg;
+    size_t off_w = 0, off_pa = 0, off_pb = 0, off_counts = 0, off_totals = 0, off_segs = 0,
+           off_tiles = 0, bytes = 0;
+};
+
+Layout make_layout(const SortProblem& p) {
+    Layout L;
+    L.nseg = (uint32_t)(p.seg_off.size() - 1);
+    L.total = p.seg_off.back();
+    L.segs.resize(L.nseg);
+    for (uint32_t s = 0; s < L.nseg; ++s) {
+        SegInfo si;
+        si.start = p.seg_off[s];
+        si.len = p.seg_off[s + 1] - p.seg_off[s];
+        si.ntiles = (uint32_t)((si.len + kTile - 1) / kTile);
+        si.tile0 = L.ntiles;
+        si.cnt_base = L.ncounts;
+        L.ncounts += 256ull * si.ntiles;
+        L.ntiles += si.ntiles;
+        for (uint32_t t = 0; t < si.ntiles; ++t) L.tile_seg.push_back(s);
+        L.segs[s] = si;
+    }
+    size_t o = 0;
+    L.off_w = o;       o = align_up(o + sizeof(uint64_t) * L.total);
+    L.off_pa = o;      o = align_up(o + sizeof(uint32_t) * L.total);
+    L.off_pb = o;      o = align_up(o + sizeof(uint32_t) * L.total);
+    L.off_counts = o;  o = align_up(o + sizeof(uint32_t) * (L.ncounts ? L.ncounts : 1));
+    L.off_totals = o;  o = align_up(o + sizeof(uint32_t) * 256 * (L.nseg ? L.nseg : 1));
+    L.off_segs = o;    o = align_up(o + sizeof(SegInfo) * (L.nseg ? L.nseg : 1));
+    L.off_tiles = o;   o = align_up(o + sizeof(uint32_t) * (L.ntiles ? L.ntiles : 1));
+    L.bytes = o;
+    return L;
+}
+
+unsigned grid_stride_blocks(uint64_t work) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (work + 255) / 256;
+    const uint64_t cap = (uint64_t)sms * 8;
+    return (unsigned)std::max<uint64_t>(1, std::min(want, cap));
+}
+
+}  // namespace
+
+size_t sort_scratch_bytes(const SortProblem& p) { return make_layout(p).bytes; }
+
+int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
+    if (p.seg_off.size() < 2 || p.key_bits < 1 || p.key_bits > 128) return HC_ERR_ARG;
+    Layout L = make_layout(p);
+    if (L.total == 0) return HC_OK;
+    if (L.total > 0xFFFFFFFFull) return HC_ERR_ARG;
+    char* base = static_cast<char*>(scratch);
+    uint64_t* wtmp = reinterpret_cast<uint64_t*>(base + L.off_w);
+    uint32_t* pa = reinterpret_cast<uint32_t*>(base + L.off_pa);
+    uint32_t* pb = reinterpret_cast<uint32_t*>(base + L.off_pb);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(base + L.off_counts);
+    uint32_t* totals = reinterpret_cast<uint32_t*>(base + L.off_totals);
+    SegInfo* segs = reinterpret_cast<SegInfo*>(base + L.off_segs);
+    uint32_t* tile_seg = reinterpret_cast<uint32_t*>(base + L.off_tiles);
+
+    cudaError_t e;
+    e = cudaMemcpyAsync(segs, L.segs.data(), sizeof(SegInfo) * L.nseg, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return HC_ERR_CUDA;
+    if (L.ntiles) {
+        e = cudaMemcpyAsync(tile_seg, L.tile_seg.data(), sizeof(uint32_t) * L.ntiles,
+                            cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return HC_ERR_CUDA;
+    }
+    const size_t dyn_smem = (sizeof(uint64_t) + sizeof(uint32_t)) * kTile;
+    e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn_smem);
+    if (e != cudaSuccess) return HC_ERR_CUDA;
+
+    const int digits = (int)((p.key_bits + 7) / 8);
+    const int lo_passes = std::min(digits, 8);
+    const int hi_passes = std::max(digits - 8, 0);
+    // word buffers written in sequence: each lo pass, the hi gather, each hi
+    // pass; alternate so that the last write lands in out_hi.
+    const int writes = lo_passes + 1 + hi_passes;
+    uint64_t* wbuf[2] = {p.out_hi, wtmp};
+    int wnext = (writes % 2 == 1) ? 0 : 1;
+    uint32_t* pbuf[2] = {pa, pb};
+    int pnext = 0;
+
+    const uint64_t* cur_w = p.lo;
+    const uint32_t* cur_p = nullptr;
+    const dim3 scan_grid(256, L.nseg);
+    auto run_pass = [&](int digit) -> int {
+        const int shift = (digit & 7) * 8;
+        if (L.ntiles) {
+            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cur_w, shift, tile_seg, segs, counts);
+            scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
+            uint64_t* wd = wbuf[wnext];
+            uint32_t* pd = pbuf[pnext];
+            scatter_kernel<<<L.ntiles, kThreads, dyn_smem, s>>>(cur_w, cur_p, wd, pd, shift,
+                                                                tile_seg, segs, counts, totals);
+            if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
+            cur_w = wd;
+            cur_p = pd;
+            wnext ^= 1;
+            pnext ^= 1;
+        }
+        return HC_OK;
+    };
+    for (int t = 0; t < lo_passes; ++t)
+        if (int rc = run_pass(t)) return rc;
+    {
+        uint64_t* wd = wbuf[wnext];
+        gather_words_kernel<<<grid_stride_blocks(L.total), 256, 0, s>>>(p.hi, cur_p, wd, L.total);
+        if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
+        cur_w = wd;
+        wnext ^= 1;
+    }
+    for (int t = 8; t < 8 + hi_passes; ++t)
+        if (int rc = run_pass(t)) return rc;
+    if (cur_w != p.out_hi) return HC_ERR_STATE;  // buffer bookkeeping broken
+    gather_final_kernel<<<grid_stride_blocks(L.total), 256, 0, s>>>(p.lo, p.ids, cur_p, p.out_lo,
+                                                                    p.out_ids, L.total);
+    if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
+    return HC_OK;
+}
+
+}  // namespace hc

@@ -1,0 +1,292 @@
+"""Python binding of libhc.so (include/hc.h): the same entry points, with
+torch tensors in place of raw pointers.
+
+Only argument marshalling happens here: every step of the path runs in the
+library's CUDA kernels.  torch provides device memory and streams.  There is
+no fallback: if libhc.so is missing or fails to load, every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhc.so")
+
+HC_OK, HC_PENDING = 0, 1
+HC_ERR_ARG, HC_ERR_OOM, HC_ERR_CUDA, HC_ERR_BUDGET = -1, -2, -3, -4
+HC_ERR_TIMEOUT, HC_ERR_DEVICE_STATUS, HC_ERR_STATE = -5, -6, -7
+HC_U8, HC_F32 = 0, 1
+
+
+class HCError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (what, hc_strerror(status), status))
+
+
+class _BuildParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("d", ctypes.c_uint32), ("curves", ctypes.c_uint32),
+                ("dims_per_curve", ctypes.c_uint32), ("bits", ctypes.c_uint32),
+                ("dtype", ctypes.c_int), ("dim_map", ctypes.POINTER(ctypes.c_uint32)),
+                ("partitions", ctypes.c_uint32)]
+
+
+class _IndexInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("d", ctypes.c_uint32), ("curves", ctypes.c_uint32),
+                ("dims_per_curve", ctypes.c_uint32), ("partitions", ctypes.c_uint32),
+                ("lists", ctypes.c_uint32), ("dtype", ctypes.c_int),
+                ("keys_hi_dev", ctypes.c_void_p), ("keys_lo_dev", ctypes.c_void_p),
+                ("ids_dev", ctypes.c_void_p), ("db_dev", ctypes.c_void_p)]
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_u32, _u64, _i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+
+
+def lib():
+    """The loaded libhc.so; raises if it is not built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhc.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.hc_strerror.restype = ctypes.c_char_p
+        L.hc_strerror.argtypes = [ctypes.c_int]
+        L.hc_build.argtypes = [_vp, ctypes.POINTER(_BuildParams), _vp, ctypes.POINTER(_vp)]
+        L.hc_build_host.argtypes = [_vp, ctypes.POINTER(_BuildParams), _vp, ctypes.POINTER(_vp)]
+        L.hc_query.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]
+        L.hc_query_host.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]
+        L.hc_free.argtypes = [_vp]
+        L.hc_free.restype = None
+        L.hc_index_describe.argtypes = [_vp, ctypes.POINTER(_IndexInfo), _vp]
+        L.hc_index_copy_lists.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.hc_hilbert_keys.argtypes = [_vp, ctypes.c_int, _u64, _u32, _u32, _u32, _vp, _vp, _vp,
+                                      _vp]
+        L.hc_sort_keys.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _vp]
+        L.hc_query_positions.argtypes = [_vp, _vp, _u32, _vp, _vp]
+        L.hc_bruteforce.argtypes = [_vp, ctypes.c_int, _u64, _u32, _vp, _u32, _u32, _vp, _vp, _vp]
+        L.hc_debug_fail_alloc.argtypes = [ctypes.c_long]
+        L.hc_debug_fail_alloc.restype = None
+        _LIB = L
+    return _LIB
+
+
+def hc_strerror(status):
+    return lib().hc_strerror(int(status)).decode()
+
+
+def _check(rc, what):
+    if rc != HC_OK:
+        raise HCError(rc, what)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t):
+    if t.dtype == torch.uint8:
+        return HC_U8
+    if t.dtype == torch.float32:
+        return HC_F32
+    raise TypeError("vectors must be uint8 or float32, got %s" % t.dtype)
+
+
+def _dev(t, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dim_map_arr(dim_map, curves, m):
+    if dim_map is None:
+        return None, None
+    dm = np.ascontiguousarray(np.asarray(dim_map, dtype=np.uint32).reshape(curves * m))
+    return dm, dm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+class Index:
+    """An hc_index handle; keeps the database tensor alive while it exists."""
+
+    def __init__(self, handle, db, params):
+        self.handle = handle
+        self.db = db
+        self.dtype = params.dtype
+        self.d = params.d
+        self.n = params.n
+        self.curves = params.curves
+        self.m = params.dims_per_curve
+        self.partitions = max(1, params.partitions)
+        self.lists = self.curves * self.partitions
+
+    def free(self):
+        if self.handle:
+            lib().hc_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _params(n, d, dtype, curves, m, dim_map, partitions):
+    p = _BuildParams()
+    p.n, p.d, p.curves, p.dims_per_curve, p.bits = n, d, curves, m, 8
+    p.dtype = dtype
+    dm, dm_p = _dim_map_arr(dim_map, curves, m)
+    p.dim_map = dm_p
+    p.partitions = partitions
+    return p, dm
+
+
+def hc_build(db, curves=8, dims_per_curve=16, dim_map=None, partitions=1, stream=None):
+    """Algorithm 1 on the GPU over a (n, d) CUDA tensor (not copied)."""
+    n, d = db.shape
+    p, keep = _params(n, d, _dtype_code(db), curves, dims_per_curve, dim_map, partitions)
+    h = ctypes.c_void_p()
+    _check(lib().hc_build(_dev(db, "db"), ctypes.byref(p), _stream(stream), ctypes.byref(h)),
+           "hc_build")
+    del keep
+    return Index(h, db, p)
+
+
+def hc_build_host(db_host, curves=8, dims_per_curve=16, dim_map=None, partitions=1, stream=None):
+    """hc_build from a host array (numpy or CPU tensor); the library copies it."""
+    arr = db_host.numpy() if isinstance(db_host, torch.Tensor) else np.asarray(db_host)
+    arr = np.ascontiguousarray(arr)
+    dtype = HC_U8 if arr.dtype == np.uint8 else (HC_F32 if arr.dtype == np.float32 else None)
+    if dtype is None:
+        raise TypeError("vectors must be uint8 or float32")
+    n, d = arr.shape
+    p, keep = _params(n, d, dtype, curves, dims_per_curve, dim_map, partitions)
+    h = ctypes.c_void_p()
+    _check(lib().hc_build_host(arr.ctypes.data_as(_vp), ctypes.byref(p), _stream(stream),
+                               ctypes.byref(h)), "hc_build_host")
+    del keep
+    return Index(h, None, p)
+
+
+def _dist_dtype(index_dtype):
+    return torch.float32 if index_dtype == HC_F32 else torch.int32
+
+
+def hc_query(index, q, k, p, out_ids=None, out_dist=None, stream=None):
+    """Algorithm 2 for a (nq, d) CUDA tensor of queries; returns (ids, dist)."""
+    nq = q.shape[0]
+    if out_ids is None:
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=_dist_dtype(index.dtype), device=q.device)
+    if nq:
+        _check(lib().hc_query(index.handle, _dev(q, "q"), nq, k, p, _dev(out_ids, "out_ids"),
+                              _dev(out_dist, "out_dist"), _stream(stream)), "hc_query")
+    return out_ids, out_dist
+
+
+def hc_query_host(index, q_host, k, p, out_ids=None, out_dist=None, stream=None):
+    """hc_query from host buffers (numpy or CPU tensors, pinned or not)."""
+    if isinstance(q_host, torch.Tensor):
+        qa = q_host
+        nq = qa.shape[0]
+        qptr = qa.data_ptr()
+    else:
+        qa = np.ascontiguousarray(q_host)
+        nq = qa.shape[0]
+        qptr = qa.ctypes.data
+    if out_ids is None:
+        out_ids = torch.empty((nq, k), dtype=torch.int32)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=_dist_dtype(index.dtype))
+    if nq:
+        _check(lib().hc_query_host(index.handle, ctypes.c_void_p(qptr), nq, k, p,
+                                   ctypes.c_void_p(out_ids.data_ptr()),
+                                   ctypes.c_void_p(out_dist.data_ptr()), _stream(stream)),
+               "hc_query_host")
+    return out_ids, out_dist
+
+
+def hc_free(index):
+    index.free()
+
+
+def hc_index_describe(index):
+    """(info dict, list_off numpy array); the device arrays stay owned by the index."""
+    info = _IndexInfo()
+    off = np.zeros(index.lists + 1, np.uint64)
+    _check(lib().hc_index_describe(index.handle, ctypes.byref(info), off.ctypes.data_as(_vp)),
+           "hc_index_describe")
+    d = {f: getattr(info, f) for f, _ in _IndexInfo._fields_}
+    return d, off
+
+
+def hc_index_copy_lists(index, stream=None):
+    """Copies of the sorted lists: (keys_hi, keys_lo, ids) as CUDA tensors
+    (int64, int64, int32; the key words are uint64 bit patterns) and the list
+    offsets (numpy uint64)."""
+    info, off = hc_index_describe(index)
+    total = int(off[-1])
+    hi = torch.empty(total, dtype=torch.int64, device="cuda")
+    lo = torch.empty(total, dtype=torch.int64, device="cuda")
+    ids = torch.empty(total, dtype=torch.int32, device="cuda")
+    if total:
+        _check(lib().hc_index_copy_lists(index.handle, _dev(hi, "hi"), _dev(lo, "lo"),
+                                         _dev(ids, "ids"), _stream(stream)),
+               "hc_index_copy_lists")
+    return hi, lo, ids, off
+
+
+def hc_hilbert_keys(x, curves, dims_per_curve, dim_map=None, stream=None):
+    """Extended-keys of every (vector, curve): two (count, curves) int64
+    tensors holding the uint64 words (hi, lo)."""
+    count, d = x.shape
+    hi = torch.empty((count, curves), dtype=torch.int64, device=x.device)
+    lo = torch.empty((count, curves), dtype=torch.int64, device=x.device)
+    dm, dm_p = _dim_map_arr(dim_map, curves, dims_per_curve)
+    if count:
+        _check(lib().hc_hilbert_keys(_dev(x, "x"), _dtype_code(x), count, d, curves,
+                                     dims_per_curve, dm_p, _dev(hi, "hi"), _dev(lo, "lo"),
+                                     _stream(stream)), "hc_hilbert_keys")
+    del dm
+    return hi, lo
+
+
+def hc_sort_keys(hi, lo, ids, seg_off, key_bits=128, stream=None):
+    """Stable in-place radix sort by 128-bit key within segments."""
+    off = np.ascontiguousarray(np.asarray(seg_off, dtype=np.uint64))
+    _check(lib().hc_sort_keys(_dev(hi, "hi"), _dev(lo, "lo"), _dev(ids, "ids"),
+                              off.ctypes.data_as(_vp), len(off) - 1, key_bits, _stream(stream)),
+           "hc_sort_keys")
+
+
+def hc_query_positions(index, q, stream=None):
+    """lower_bound position of each query in each list: (nq, lists) int64."""
+    nq = q.shape[0]
+    pos = torch.empty((nq, index.lists), dtype=torch.int64, device=q.device)
+    if nq:
+        _check(lib().hc_query_positions(index.handle, _dev(q, "q"), nq, _dev(pos, "pos"),
+                                        _stream(stream)), "hc_query_positions")
+    return pos
+
+
+def hc_bruteforce(db, q, k, stream=None):
+    """Exact kNN (Eq. 3) on the GPU: (ids, dist)."""
+    n, d = db.shape
+    nq = q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+    dist = torch.empty((nq, k), dtype=_dist_dtype(_dtype_code(db)), device=q.device)
+    if nq:
+        _check(lib().hc_bruteforce(_dev(db, "db"), _dtype_code(db), n, d, _dev(q, "q"), nq, k,
+                                   _dev(ids, "ids"), _dev(dist, "dist"), _stream(stream)),
+               "hc_bruteforce")
+    return ids, dist
+
+
+def hc_debug_fail_alloc(after):
+    lib().hc_debug_fail_alloc(int(after))

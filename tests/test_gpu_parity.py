@@ -1,0 +1,361 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+uint8: bit-exact (keys, sorted lists, positions, ids, int32 distances).
+float32: distances within 1e-5 relative of the oracle's double sums; id sets
+equal except inside the tie band at the k-th distance.
+Sizes span several 4096-record sort tiles and 32-row gather chunks with
+ragged tails; edge cases: p = 0, p beyond the list, k beyond the candidates,
+duplicate rows, one query, queries not a multiple of the block's 8 warps.
+"""
+import numpy as np
+import pytest
+
+from helpers import compare_f32, dev, u64
+from oracle import oracle as O
+from paper_1209_0410_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1209_0410_gb300 import hc as _hc
+    _hc.lib()
+    return _hc
+
+
+def sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def make_case(n, nq, d=128, seed=41, dtype="u8"):
+    db = datagen.make_db(n, d, seed=seed)
+    q = datagen.make_queries(db, nq, seed=seed + 7)
+    if dtype == "f32":
+        db, q = datagen.to_f32(db), datagen.to_f32(q)
+    return db, q
+
+
+# ------------------------------------------------------------------ K1
+@pytest.mark.parametrize("m,curves,mapped", [(16, 8, False), (16, 8, True), (8, 16, False),
+                                             (5, 3, True), (1, 4, False), (16, 1, False),
+                                             (13, 2, True)])
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_hilbert_keys_bit_exact(hc, m, curves, mapped, dtype):
+    rng = np.random.default_rng(m * 100 + curves)
+    d = 128
+    x = rng.integers(0, 256, size=(5003, d), dtype=np.uint8)
+    x[0] = 0
+    x[1] = 255
+    x[2, ::2] = 255
+    if dtype == "f32":
+        x = datagen.to_f32(x)
+        x[3] = np.float32(-0.5)
+        x[4] = np.float32(1.7)
+        x[5, :7] = np.array([np.nan, np.inf, -np.inf, 0.5 / 255, 1.5 / 255, 254.5 / 255, 1.0],
+                            np.float32)
+        x[6:200] = rng.random((194, d), dtype=np.float32) * np.float32(1.2) - np.float32(0.1)
+    dim_map = rng.permutation(d)[:curves * m].astype(np.uint32).reshape(curves, m) if mapped \
+        else None
+    hi, lo = hc.hc_hilbert_keys(dev(x), curves, m, dim_map)
+    sync()
+    ohi, olo = O.query_keys(x, curves, m, dim_map)
+    assert np.array_equal(u64(hi), ohi)
+    assert np.array_equal(u64(lo), olo)
+
+
+# ------------------------------------------------------------------ K2
+@pytest.mark.parametrize("case", ["random", "duplicates", "narrow", "ragged", "reversed_ids"])
+def test_sort_keys_matches_stable_sort(hc, case):
+    import torch
+    rng = np.random.default_rng(["random", "duplicates", "narrow", "ragged", "reversed_ids"].index(case) + 1)
+    sizes = {"random": [30000], "duplicates": [20000, 5000], "narrow": [12289],
+             "ragged": [0, 1, 4095, 4096, 4097, 9000, 33, 0, 2],
+             "reversed_ids": [8192, 7000]}[case]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    total = int(off[-1])
+    key_bits = 128
+    hi = rng.integers(0, 2**63, size=total, dtype=np.uint64) * np.uint64(2) + \
+        rng.integers(0, 2, size=total, dtype=np.uint64)
+    lo = rng.integers(0, 2**63, size=total, dtype=np.uint64) * np.uint64(2) + \
+        rng.integers(0, 2, size=total, dtype=np.uint64)
+    if case == "duplicates":
+        pool_hi = hi[:37].copy()
+        pool_lo = lo[:37].copy()
+        pick = rng.integers(0, 37, size=total)
+        hi, lo = pool_hi[pick], pool_lo[pick]
+    if case == "narrow":
+        key_bits = 40
+        hi[:] = 0
+        lo &= np.uint64((1 << 40) - 1)
+    ids = np.arange(total, dtype=np.uint32)
+    if case == "reversed_ids":
+        ids = ids[::-1].copy()
+        hi[:] = hi[:16].repeat(total // 16 + 1)[:total]
+        lo[:] = 7
+    th = torch.from_numpy(hi.view(np.int64)).cuda()
+    tl = torch.from_numpy(lo.view(np.int64)).cuda()
+    ti = torch.from_numpy(ids.view(np.int32)).cuda()
+    hc.hc_sort_keys(th, tl, ti, off, key_bits)
+    sync()
+    gh, gl, gi = u64(th), u64(tl), ti.cpu().numpy().view(np.uint32)
+    for s in range(len(sizes)):
+        a, b = int(off[s]), int(off[s + 1])
+        order = np.lexsort((np.arange(b - a), lo[a:b], hi[a:b]))  # stable by key
+        assert np.array_equal(gh[a:b], hi[a:b][order])
+        assert np.array_equal(gl[a:b], lo[a:b][order])
+        assert np.array_equal(gi[a:b], ids[a:b][order])
+
+
+# ------------------------------------------------------- Algorithm 1 lists
+BUILD_CASES = [
+    dict(n=10007, parts=1, dtype="u8", mapped=False, curves=8, m=16, d=128),
+    dict(n=20000, parts=3, dtype="u8", mapped=False, curves=8, m=16, d=128),
+    dict(n=9000, parts=1, dtype="u8", mapped=True, curves=8, m=16, d=128),
+    dict(n=12000, parts=2, dtype="f32", mapped=False, curves=8, m=16, d=128),
+    dict(n=7001, parts=1, dtype="u8", mapped=False, curves=4, m=16, d=64),
+    dict(n=6000, parts=1, dtype="u8", mapped=False, curves=16, m=16, d=256),
+    dict(n=5000, parts=1, dtype="u8", mapped=False, curves=10, m=6, d=64),
+    dict(n=5, parts=1, dtype="u8", mapped=False, curves=8, m=16, d=128),
+    dict(n=3, parts=4, dtype="u8", mapped=False, curves=2, m=16, d=32),
+]
+
+
+def build_both(hc, c):
+    db, _ = make_case(c["n"], 1, d=c["d"], dtype=c["dtype"], seed=c["n"])
+    rng = np.random.default_rng(c["n"])
+    dim_map = rng.permutation(c["d"])[:c["curves"] * c["m"]].astype(np.uint32).reshape(
+        c["curves"], c["m"]) if c["mapped"] else None
+    idx = hc.hc_build(dev(db), curves=c["curves"], dims_per_curve=c["m"], dim_map=dim_map,
+                      partitions=c["parts"])
+    oidx = O.build(db, curves=c["curves"], m=c["m"], dim_map=dim_map, ell=c["parts"])
+    return db, dim_map, idx, oidx
+
+
+@pytest.mark.parametrize("c", BUILD_CASES, ids=lambda c: "n%d_l%d_%s_c%d_m%d_d%d%s" % (
+    c["n"], c["parts"], c["dtype"], c["curves"], c["m"], c["d"], "_map" if c["mapped"] else ""))
+def test_build_lists_bit_exact(hc, c):
+    _, _, idx, oidx = build_both(hc, c)
+    hi, lo, ids, off = hc.hc_index_copy_lists(idx)
+    sync()
+    assert np.array_equal(off, oidx.list_off)
+    assert np.array_equal(u64(hi), oidx.keys_hi)
+    assert np.array_equal(u64(lo), oidx.keys_lo)
+    assert np.array_equal(ids.cpu().numpy().view(np.uint32), oidx.ids)
+    idx.free()
+
+
+@pytest.mark.parametrize("c", BUILD_CASES[:4])
+def test_positions_bit_exact(hc, c):
+    db, dim_map, idx, oidx = build_both(hc, c)
+    _, q = make_case(c["n"], 203, d=c["d"], dtype=c["dtype"], seed=c["n"])
+    pos = hc.hc_query_positions(idx, dev(q))
+    sync()
+    _, _, opos = O.search(oidx, db, q, 1, 0, return_pos=True)
+    assert np.array_equal(pos.cpu().numpy(), opos)
+    idx.free()
+
+
+# ------------------------------------------------------- Algorithm 2 queries
+@pytest.mark.parametrize("k,p", [(10, 64), (1, 5), (33, 17), (64, 50), (100, 40), (128, 200),
+                                 (10, 0), (10, 1), (7, 1_000_000), (10, 3)])
+def test_query_u8_bit_exact(hc, k, p):
+    n, nq = 20011, 301
+    db, q = make_case(n, nq, seed=5)
+    idx = hc.hc_build(dev(db))
+    ids, dist = hc.hc_query(idx, dev(q), k, p)
+    sync()
+    oidx = O.build(db, curves=8, m=16)
+    rids, rdist = O.search(oidx, db, q, k, p)
+    assert np.array_equal(ids.cpu().numpy(), rids)
+    assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+    idx.free()
+
+
+@pytest.mark.parametrize("d,curves,m,k,p", [(64, 4, 16, 10, 40), (256, 16, 16, 10, 30),
+                                            (32, 2, 16, 5, 20), (48, 3, 16, 10, 25),
+                                            (128, 12, 10, 10, 33)])
+def test_query_u8_other_shapes(hc, d, curves, m, k, p):
+    n, nq = 9001, 77
+    db, q = make_case(n, nq, d=d, seed=d)
+    idx = hc.hc_build(dev(db), curves=curves, dims_per_curve=m)
+    ids, dist = hc.hc_query(idx, dev(q), k, p)
+    sync()
+    oidx = O.build(db, curves=curves, m=m)
+    rids, rdist = O.search(oidx, db, q, k, p)
+    assert np.array_equal(ids.cpu().numpy(), rids)
+    assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+    idx.free()
+
+
+@pytest.mark.parametrize("parts,scheme_p", [(2, 64), (3, 20), (8, 10), (5, 100000)])
+def test_query_partitioned_bit_exact(hc, parts, scheme_p):
+    n, nq, k = 24000, 150, 10
+    db, q = make_case(n, nq, seed=parts)
+    idx = hc.hc_build(dev(db), partitions=parts)
+    ids, dist = hc.hc_query(idx, dev(q), k, scheme_p)
+    sync()
+    oidx = O.build(db, curves=8, m=16, ell=parts)
+    rids, rdist = O.search(oidx, db, q, k, scheme_p)
+    assert np.array_equal(ids.cpu().numpy(), rids)
+    assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+    idx.free()
+
+
+@pytest.mark.parametrize("d,k,p,parts", [(128, 10, 64, 1), (64, 10, 50, 1), (256, 10, 30, 1),
+                                         (128, 100, 40, 1), (128, 10, 64, 3), (16, 3, 9, 1)])
+def test_query_f32_within_tolerance(hc, d, k, p, parts):
+    n, nq = 15013, 211
+    curves = max(1, d // 16)
+    db, q = make_case(n, nq, d=d, seed=d + 1, dtype="f32")
+    idx = hc.hc_build(dev(db), curves=curves, dims_per_curve=16, partitions=parts)
+    ids, dist = hc.hc_query(idx, dev(q), k, p)
+    sync()
+    oidx = O.build(db, curves=curves, m=16, ell=parts)
+    rids, rdist = O.search(oidx, db, q, k, p)
+    probs = compare_f32(ids.cpu().numpy(), dist.cpu().numpy(), rids, rdist)
+    assert not probs, probs[:5]
+    idx.free()
+
+
+def test_f32_index_has_u8_windows(hc):
+    """x = u8/255 in float32 quantises back to the bytes: same keys and lists."""
+    n = 8000
+    db, _ = make_case(n, 1, seed=77)
+    a = hc.hc_build(dev(db))
+    b = hc.hc_build(dev(datagen.to_f32(db)))
+    ha, la, ia, _ = hc.hc_index_copy_lists(a)
+    hb, lb, ib, _ = hc.hc_index_copy_lists(b)
+    sync()
+    assert np.array_equal(u64(ha), u64(hb)) and np.array_equal(u64(la), u64(lb))
+    assert np.array_equal(ia.cpu().numpy(), ib.cpu().numpy())
+
+
+def test_duplicate_rows_rank_lower_id_first(hc):
+    rng = np.random.default_rng(3)
+    base = rng.integers(0, 256, size=(1500, 128), dtype=np.uint8)
+    db = np.concatenate([base, base, base, base])
+    q = base[:100].copy()
+    idx = hc.hc_build(dev(db))
+    ids, dist = hc.hc_query(idx, dev(q), 4, 64)
+    sync()
+    oidx = O.build(db, curves=8, m=16)
+    rids, rdist = O.search(oidx, db, q, 4, 64)
+    assert np.array_equal(ids.cpu().numpy(), rids)
+    assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+    g = ids.cpu().numpy()
+    for i in range(100):
+        assert g[i].tolist() == [i, i + 1500, i + 3000, i + 4500]
+
+
+@pytest.mark.parametrize("nq", [0, 1, 7, 9, 1000])
+def test_query_batch_sizes(hc, nq):
+    n = 6000
+    db, q = make_case(n, max(nq, 1), seed=nq + 3)
+    q = q[:nq]
+    idx = hc.hc_build(dev(db))
+    ids, dist = hc.hc_query(idx, dev(q), 10, 32)
+    sync()
+    assert ids.shape == (nq, 10)
+    if nq:
+        oidx = O.build(db, curves=8, m=16)
+        rids, rdist = O.search(oidx, db, q, 10, 32)
+        assert np.array_equal(ids.cpu().numpy(), rids)
+        assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+
+
+def test_query_host_matches_device(hc):
+    n, nq = 8000, 123
+    db, q = make_case(n, nq, seed=9)
+    idx = hc.hc_build_host(db)
+    ids_h, dist_h = hc.hc_query_host(idx, q, 10, 50)
+    oidx = O.build(db, curves=8, m=16)
+    rids, rdist = O.search(oidx, db, q, 10, 50)
+    assert np.array_equal(ids_h.numpy(), rids)
+    assert np.array_equal(dist_h.numpy(), O.int32_dist(rdist))
+    # twice more, with a smaller and a larger batch (staging reuse / growth)
+    for m in (17, nq):
+        ids_h, dist_h = hc.hc_query_host(idx, q[:m], 10, 50)
+        assert np.array_equal(ids_h.numpy(), rids[:m])
+
+
+# ------------------------------------------------------------- exact kNN
+@pytest.mark.parametrize("dtype,k,d", [("u8", 10, 128), ("u8", 100, 128), ("u8", 1, 64),
+                                       ("f32", 10, 128), ("f32", 33, 256), ("u8", 128, 32)])
+def test_bruteforce_matches_oracle(hc, dtype, k, d):
+    n, nq = 7013, 61
+    db, q = make_case(n, nq, d=d, seed=k, dtype=dtype)
+    ids, dist = hc.hc_bruteforce(dev(db), dev(q), k)
+    sync()
+    rids, rdist = O.bruteforce(db, q, k)
+    if dtype == "u8":
+        assert np.array_equal(ids.cpu().numpy(), rids)
+        assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+    else:
+        probs = compare_f32(ids.cpu().numpy(), dist.cpu().numpy(), rids, rdist)
+        assert not probs, probs[:5]
+
+
+def test_full_depth_query_equals_bruteforce(hc):
+    n, nq = 4000, 64
+    db, q = make_case(n, nq, seed=12)
+    idx = hc.hc_build(dev(db))
+    ids, dist = hc.hc_query(idx, dev(q), 10, n)
+    bids, bdist = hc.hc_bruteforce(dev(db), dev(q), 10)
+    sync()
+    assert np.array_equal(ids.cpu().numpy(), bids.cpu().numpy())
+    assert np.array_equal(dist.cpu().numpy(), bdist.cpu().numpy())
+
+
+# ------------------------------------------------------------- error paths
+def test_invalid_arguments_are_rejected(hc):
+    import torch
+    db, q = make_case(2000, 4, seed=1)
+    idx = hc.hc_build(dev(db))
+    tq = dev(q)
+    for k, p in ((0, 10), (129, 10), (10, (1 << 30) + 1)):
+        with pytest.raises(hc.HCError) as e:
+            hc.hc_query(idx, tq, k, p, out_ids=torch.empty((4, max(k, 1)), dtype=torch.int32,
+                                                           device="cuda"),
+                        out_dist=torch.empty((4, max(k, 1)), dtype=torch.int32, device="cuda"))
+        assert e.value.status == hc.HC_ERR_ARG
+    # a host buffer where a device buffer is required
+    rc = hc.lib().hc_query(idx.handle, q.ctypes.data, 4, 10, 10,
+                           torch.empty((4, 10), dtype=torch.int32, device="cuda").data_ptr(),
+                           torch.empty((4, 10), dtype=torch.int32, device="cuda").data_ptr(), None)
+    assert rc == hc.HC_ERR_ARG
+    # build parameter checks
+    with pytest.raises(hc.HCError):
+        hc.hc_build(dev(db), curves=9)                 # 9*16 > d
+    with pytest.raises(hc.HCError):
+        hc.hc_build(dev(db), dims_per_curve=17)
+    with pytest.raises(hc.HCError):
+        hc.hc_build(dev(db[:, :120].copy()))           # rows not a multiple of 16 bytes
+    with pytest.raises(hc.HCError):
+        hc.hc_build(dev(db), curves=8, partitions=33)  # 264 lists
+
+
+def test_injected_allocation_failure_reports_oom(hc):
+    db, q = make_case(3000, 5, seed=2)
+    tdb = dev(db)
+    for after in range(0, 6):
+        hc.hc_debug_fail_alloc(after)
+        try:
+            idx = hc.hc_build(tdb)
+        except hc.HCError as e:
+            assert e.status == hc.HC_ERR_OOM
+        else:
+            idx.free()
+        finally:
+            hc.hc_debug_fail_alloc(-1)
+    # the library is usable afterwards
+    idx = hc.hc_build(tdb)
+    ids, _ = hc.hc_query(idx, dev(q), 5, 16)
+    sync()
+    oidx = O.build(db, curves=8, m=16)
+    rids, _ = O.search(oidx, db, q, 5, 16)
+    assert np.array_equal(ids.cpu().numpy(), rids)
