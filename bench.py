@@ -1,0 +1,432 @@
+#!/usr/bin/env python3
+"""Benchmark of the Hypercurves hot path on GB300.
+
+One step = the whole path over one batch of synthetic input, with the inputs
+already resident in HBM:
+  hc_build  Algorithm 1: Hilbert keys of N rows x 8 curves + radix sort
+  hc_query  Algorithm 2 for Q queries: keys, lower_bound, window gathers,
+            exact distances, top-k merged over curves
+value = queries answered per second of step time (whole job, all ranks).
+
+Workload (default): N = 10,000,000 uint8 rows of 128 dims from the seeded
+64-cluster Gaussian mixture (sigma 20) standing in for SIFT, Q = 100,000
+queries (rows + N(0, 8)), 8 curves of 16 dims, p = 128 per side, k = 10.
+The database (1.28 GB) and the index (1.6 GB) are larger than L2, so no L2
+flush is needed between steps.
+
+`--impl reference` times the CPU oracle instead (the reference arm: a
+deliberately plain program), on a bounded sample scaled to the workload.
+
+Multi-GPU: one process per GPU under torchrun; every rank runs an
+independent replica (its own index and query batch), with no collective on
+the data path (weak scaling); only the step timings are reduced (max).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("queries/s at fixed recall@10, 10M×128-d uint8, 8 curves; % HBM peak; "
+          "p99 latency")
+UNIT = "queries/s"
+DATA = ("synthetic: seeded 64-cluster isotropic Gaussian mixture (centres uniform in "
+        "[0,255], sigma 20, rounded and clipped) standing in for 128-d SIFT; queries are "
+        "database rows plus N(0, 8) noise")
+QUERY_SOURCES = ["paper_1209_0410_gb300/csrc/query.cu", "paper_1209_0410_gb300/csrc/hc_topk.cuh",
+                 "paper_1209_0410_gb300/csrc/hc_device.cuh"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["hc", "reference"], default="hc")
+    ap.add_argument("--n-db", type=int, default=10_000_000)
+    ap.add_argument("--nq", type=int, default=100_000)
+    ap.add_argument("--p", type=int, default=128)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--dtype", choices=["u8", "f32"], default="u8")
+    ap.add_argument("--sweep", default="32,128,512", help="query-only p sweep ('' = none)")
+    ap.add_argument("--recall-sample", type=int, default=2000)
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps only: no sweep, recall, e2e or CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=1_000_000,
+                    help="rows of the oracle's bounded build sample")
+    ap.add_argument("--cpu-queries", type=int, default=2000,
+                    help="queries of the oracle's bounded search sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_name(a):
+    return ("plain Hypercurves at scale: N=%d x %d-d %s, 8 curves x 16 dims, Q=%d, p=%d, k=%d; "
+            "step = index build + query batch" % (a.n_db, 128, "uint8" if a.dtype == "u8"
+                                                   else "float32 (u8/255)", a.nq, a.p, a.k))
+
+
+def make_inputs(a, rank):
+    import numpy as np
+    from paper_1209_0410_gb300 import datagen
+    db = datagen.make_db(a.n_db, 128, seed=datagen.SEED_DB)
+    q = datagen.make_queries(db, a.nq, seed=datagen.SEED_QUERIES + 1000 * rank)
+    if a.dtype == "f32":
+        db, q = datagen.to_f32(db), datagen.to_f32(q)
+    return np.ascontiguousarray(db), np.ascontiguousarray(q)
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(kernel_tag):
+    """Per-launch DRAM bytes from the committed ncu summary of this kernel, if
+    the summary was taken on the current source (else None)."""
+    path = os.path.join(ROOT, "profiles", "%s.md" % kernel_tag)
+    if not os.path.exists(path):
+        return None, None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != source_sha(QUERY_SOURCES):
+        return None, vals.get("source_sha")
+    try:
+        return float(vals["dram_bytes_per_launch_scaled"]), vals.get("source_sha")
+    except (KeyError, ValueError):
+        return None, vals.get("source_sha")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu),
+                                          "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, st in rows for i, v in enumerate(st)
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def algorithmic_query_bytes(hc, idx, q_dev, p, k, row_bytes):
+    """Bytes the method itself must move for one query launch (per query:
+    window ids 4 B + window rows, the global binary-search probes beyond 12
+    cached levels at 16 B, the query row and k (id, distance) results)."""
+    import torch
+    pos = hc.hc_query_positions(idx, q_dev)
+    _, off = hc.hc_index_describe(idx)
+    n_list = torch.tensor((off[1:] - off[:-1]).astype("int64"), device=pos.device)
+    lo = torch.clamp(pos - p, min=0)
+    hi = torch.minimum(pos + p, n_list.unsqueeze(0))
+    windows = int((hi - lo).clamp(min=0).sum().item())
+    nq, lists = pos.shape
+    lg = sum(max(0, int(n).bit_length() - 12) for n in (off[1:] - off[:-1]).tolist())
+    return windows * (row_bytes + 4) + nq * (lg * 16 + row_bytes + k * 8), windows
+
+
+def recall_at_10(ids, dist, true_dist):
+    import torch
+    kth = true_dist[:, 9:10].to(torch.float64)
+    ok = (dist[:, :10].to(torch.float64) <= kth) & (ids[:, :10] >= 0)
+    return float(ok.sum(dim=1).clamp(max=10).to(torch.float64).mean().item() / 10.0)
+
+
+# ----------------------------------------------------------- CPU oracle leg
+def cpu_oracle_sample(a, db, q):
+    """Times the oracle (as it stands) on a bounded sample of the workload and
+    projects the whole job: build on the first cpu_rows rows (scaled
+    linearly to N) plus search of the first cpu_queries queries (scaled to Q)."""
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    rows = min(a.cpu_rows, a.n_db)
+    nqs = min(a.cpu_queries, a.nq)
+    sub = db[:rows]
+    t0 = time.perf_counter()
+    oidx = O.build(sub, curves=8, m=16, nthreads=threads)
+    t1 = time.perf_counter()
+    O.search(oidx, sub, q[:nqs], a.k, a.p, nthreads=threads)
+    t2 = time.perf_counter()
+    t_job = (t1 - t0) * (a.n_db / rows) + (t2 - t1) * (a.nq / nqs)
+    return {"value": a.nq / t_job, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": ("oracle build of the first %d rows (8 lists on up to 8 threads, %.2f s, "
+                       "scaled x%.1f to N) + search of %d queries at p=%d on %d threads "
+                       "(%.2f s, scaled x%.1f to Q); whole-job estimate %.1f s"
+                       % (rows, t1 - t0, a.n_db / rows, nqs, a.p, threads, t2 - t1,
+                          a.nq / nqs, t_job))}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    db, q = make_inputs(a, 0)
+    times = []
+    last = None
+    for i in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        last = cpu_oracle_sample(a, db, q)
+        if i >= a.warmup:
+            times.append(a.nq / last["value"])
+    t_job = statistics.mean(times)
+    value = a.nq / t_job
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": t_job * 1000.0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": a.dtype, "data": DATA,
+            "config": {"workload": workload_name(a), "n_db": a.n_db, "nq": a.nq, "p": a.p,
+                       "k": a.k, "curves": 8, "dims_per_curve": 16,
+                       "note": "each step times the oracle on a bounded sample and projects "
+                               "the whole-job time"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"],
+                             "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ GPU leg
+def run_hc(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1209_0410_gb300 import hc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    hc.lib()
+    db_np, q_np = make_inputs(a, rank)
+    row_bytes = 128 * (4 if a.dtype == "f32" else 1)
+    db = torch.from_numpy(db_np).cuda()
+    q = torch.from_numpy(q_np).cuda()
+    stream = torch.cuda.current_stream()
+    out_ids = torch.empty((a.nq, a.k), dtype=torch.int32, device="cuda")
+    out_dist = torch.empty((a.nq, a.k), dtype=torch.float32 if a.dtype == "f32" else torch.int32,
+                           device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step(ev):
+        ev[0].record(stream)
+        idx = hc.hc_build(db, 8, 16, stream=stream)
+        ev[1].record(stream)
+        hc.hc_query(idx, q, a.k, a.p, out_ids, out_dist, stream=stream)
+        ev[2].record(stream)
+        idx.free()
+
+    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(a.warmup):
+        step(mk())
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    events = [mk() for _ in range(a.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = hc.hc_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(a.steps):
+        step(events[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = hc.hc_launch_count() - launches0
+    clocks = sampler.stop() if rank == 0 else None
+
+    total_ms = t_start.elapsed_time(t_end)
+    build_ms = [e[0].elapsed_time(e[1]) for e in events]
+    query_ms = [e[1].elapsed_time(e[2]) for e in events]
+    step_ms = [e[0].elapsed_time(e[2]) for e in events]
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / a.steps
+    value = world * a.nq / (ms_per_step / 1000.0)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    idx = hc.hc_build(db, 8, 16, stream=stream)
+    torch.cuda.synchronize()
+    qbytes, windows = algorithmic_query_bytes(hc, idx, q, a.p, a.k, row_bytes)
+    q_ms = statistics.mean(query_ms)
+    peaks, peak_src = measured_peaks()
+    achieved = qbytes / (q_ms / 1000.0) / 1e9
+    traffic, _ = ncu_traffic("query_kernel")
+    roofline = {"kernel": "query_kernel (fused K1+K3+K4+K5+K6)", "bound": "hbm",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": qbytes,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
+                if peak_src == "measured" else "fallback 6.8 TB/s"}
+
+    cfg = {"workload": workload_name(a), "n_db": a.n_db, "nq": a.nq, "p": a.p, "k": a.k,
+           "curves": 8, "dims_per_curve": 16, "partitions": 1,
+           "l2": "inputs larger than L2 (database %.2f GB, index %.2f GB vs 129 MB L2)"
+                 % (a.n_db * row_bytes / 1e9, a.n_db * 8 * 20 / 1e9),
+           "build_ms": statistics.mean(build_ms), "query_ms": q_ms,
+           "query_only_qps": a.nq / (q_ms / 1000.0),
+           "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                               "p99": float(np.percentile(step_ms, 99))},
+           "window_rows_per_query": windows / a.nq}
+
+    if not a.quick and a.recall_sample > 0:
+        rs = min(a.recall_sample, a.nq)
+        tids, tdist = hc.hc_bruteforce(db, q[:rs], 10)
+        torch.cuda.synchronize()
+        cfg["recall_at_10"] = recall_at_10(out_ids[:rs], out_dist[:rs], tdist)
+        cfg["recall_sample_queries"] = rs
+        sweep = []
+        for p in [int(x) for x in a.sweep.split(",") if x.strip()]:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            hc.hc_query(idx, q, a.k, p, out_ids, out_dist, stream=stream)
+            ev[0].record(stream)
+            reps = 3
+            for _ in range(reps):
+                hc.hc_query(idx, q, a.k, p, out_ids, out_dist, stream=stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / reps
+            qb, _ = algorithmic_query_bytes(hc, idx, q, p, a.k, row_bytes)
+            sweep.append({"p": p, "query_ms": ms, "query_qps": a.nq / (ms / 1000.0),
+                          "recall_at_10": recall_at_10(out_ids[:rs], out_dist[:rs], tdist),
+                          "hbm_frac": qb / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]})
+        cfg["query_sweep"] = sweep
+    idx.free()
+
+    e2e = None
+    if not a.quick:
+        db_pin = torch.from_numpy(db_np).pin_memory()
+        q_pin = torch.from_numpy(q_np).pin_memory()
+        ids_pin = torch.empty((a.nq, a.k), dtype=torch.int32).pin_memory()
+        dist_pin = torch.empty((a.nq, a.k), dtype=out_dist.dtype).pin_memory()
+
+        def e2e_step():
+            ix = hc.hc_build_host(db_pin, 8, 16, stream=stream)
+            hc.hc_query_host(ix, q_pin, a.k, a.p, ids_pin, dist_pin, stream=stream)
+            ix.free()
+
+        for _ in range(max(1, a.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / a.steps
+        e2e = {"value": a.nq / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(db_np.nbytes + q_np.nbytes),
+               "d2h_bytes_per_step": int(ids_pin.numel() * 4 + dist_pin.numel() * 4),
+               "ms_per_step": e2e_s * 1000.0,
+               "path": "hc_build_host + hc_query_host from pinned host buffers"}
+
+    cpu = None
+    if not a.quick and not a.no_cpu_baseline and world == 1:
+        cpu = cpu_oracle_sample(a, db_np, q_np)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": a.dtype, "data": DATA,
+            "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_hc(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

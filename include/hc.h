@@ -217,6 +217,11 @@ HC_API int hc_bruteforce(const void* db_dev, hc_dtype dtype, uint64_t n, uint32_
 
 /* ------------------------------------------------------------ testing */
 
+/* hc_launch_count -- number of CUDA kernel launches the library has issued
+ * since it was loaded (all entry points, all devices).  No counterpart in the
+ * paper: it lets a caller count the kernels inside a timed region. */
+HC_API uint64_t hc_launch_count(void);
+
 /*
  * hc_debug_fail_alloc -- host-side fault injection (no counterpart in the
  * paper; it exists so that allocation-failure handling can be tested without

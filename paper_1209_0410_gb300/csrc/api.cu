@@ -27,6 +27,12 @@ struct hc_index {
     size_t st_q_cap = 0, st_out_cap = 0;
 };
 
+static std::atomic<uint64_t> g_launches{0};
+
+namespace hc {
+void count_launches(uint64_t n) { g_launches.fetch_add(n); }
+}  // namespace hc
+
 namespace {
 
 // Host-side fault injection for tests: the allocation numbered fail_after
@@ -128,16 +134,23 @@ IndexView view_of(const hc_index* x) {
     return v;
 }
 
+// The index arrays come from the stream-ordered pool; they are released in
+// order on the legacy default stream (after the work of every blocking
+// stream), so build/free cycles reuse pool memory without device syncs.
+void pool_free(void* p) {
+    if (p) cudaFreeAsync(p, cudaStreamLegacy);
+}
+
 void destroy(hc_index* x) {
     if (!x) return;
-    cudaFree(x->dim_map_dev);
-    cudaFree(x->db_owned);
-    cudaFree(x->keys_hi);
-    cudaFree(x->keys_lo);
-    cudaFree(x->ids);
-    cudaFree(x->list_off_dev);
-    cudaFree(x->st_q);
-    cudaFree(x->st_out);
+    pool_free(x->dim_map_dev);
+    pool_free(x->db_owned);
+    pool_free(x->keys_hi);
+    pool_free(x->keys_lo);
+    pool_free(x->ids);
+    pool_free(x->list_off_dev);
+    if (x->st_q) cudaFree(x->st_q);
+    if (x->st_out) cudaFree(x->st_out);
     cudaGetLastError();
     delete x;
 }
@@ -156,32 +169,33 @@ int build_index(hc_index* x, cudaStream_t s) {
     }
     const uint64_t total = x->list_off[x->lists];
     int rc;
-    if ((rc = dev_alloc((void**)&x->list_off_dev, sizeof(uint64_t) * (x->lists + 1)))) return rc;
+    keep_pool_memory();
+    if ((rc = dev_alloc_async((void**)&x->list_off_dev, sizeof(uint64_t) * (x->lists + 1), s)))
+        return rc;
     if (!x->dim_map.empty()) {
-        if ((rc = dev_alloc((void**)&x->dim_map_dev, sizeof(uint32_t) * x->dim_map.size())))
+        if ((rc = dev_alloc_async((void**)&x->dim_map_dev,
+                                  sizeof(uint32_t) * (x->dim_map.size() + 1), s)))
             return rc;
-        if ((rc = status_of(cudaMemcpyAsync(x->dim_map_dev, x->dim_map.data(),
-                                            sizeof(uint32_t) * x->dim_map.size(),
-                                            cudaMemcpyHostToDevice, s))))
+        if ((rc = status_of(upload_small(x->dim_map_dev, x->dim_map.data(),
+                                         sizeof(uint32_t) * x->dim_map.size(), s))))
             return rc;
     }
-    if ((rc = status_of(cudaMemcpyAsync(x->list_off_dev, x->list_off.data(),
-                                        sizeof(uint64_t) * (x->lists + 1), cudaMemcpyHostToDevice,
-                                        s))))
+    if ((rc = status_of(upload_small(x->list_off_dev, x->list_off.data(),
+                                     sizeof(uint64_t) * (x->lists + 1), s))))
         return rc;
-    if ((rc = dev_alloc((void**)&x->keys_hi, sizeof(uint64_t) * total))) return rc;
-    if ((rc = dev_alloc((void**)&x->keys_lo, sizeof(uint64_t) * total))) return rc;
-    if ((rc = dev_alloc((void**)&x->ids, sizeof(uint32_t) * total))) return rc;
+    if ((rc = dev_alloc_async((void**)&x->keys_hi, sizeof(uint64_t) * total, s))) return rc;
+    if ((rc = dev_alloc_async((void**)&x->keys_lo, sizeof(uint64_t) * total, s))) return rc;
+    if ((rc = dev_alloc_async((void**)&x->ids, sizeof(uint32_t) * total, s))) return rc;
 
     SortProblem sp;
     sp.seg_off = x->list_off;
+    sp.seg_off_dev = x->list_off_dev;
     sp.key_bits = 8 * P.dims_per_curve;
     sp.out_hi = x->keys_hi;
     sp.out_lo = x->keys_lo;
     sp.out_ids = x->ids;
     const size_t sort_bytes = sort_scratch_bytes(sp);
     const size_t key_bytes = (sizeof(uint64_t) * 2 + sizeof(uint32_t)) * total;
-    keep_pool_memory();
     void* scratch = nullptr;
     if ((rc = dev_alloc_async(&scratch, key_bytes + 256 + sort_bytes, s))) return rc;
     uint64_t* hi0 = static_cast<uint64_t*>(scratch);
@@ -263,7 +277,8 @@ HC_API int hc_build_host(const void* db_host, const hc_build_params* params, voi
     if (int rc = new_index(nullptr, params, out, &x)) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const size_t bytes = (size_t)params->n * row_bytes_of(params->dtype, params->d);
-    int rc = dev_alloc(&x->db_owned, bytes);
+    keep_pool_memory();
+    int rc = dev_alloc_async(&x->db_owned, bytes, s);
     if (!rc) rc = status_of(cudaMemcpyAsync(x->db_owned, db_host, bytes, cudaMemcpyHostToDevice, s));
     x->db = x->db_owned;
     if (!rc) rc = build_index(x, s);
@@ -420,15 +435,21 @@ HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
     sp.seg_off.assign(seg_off_host, seg_off_host + nseg + 1);
     sp.key_bits = key_bits;
     const size_t out_bytes = (sizeof(uint64_t) * 2 + sizeof(uint32_t)) * total;
+    const size_t off_bytes = sizeof(uint64_t) * (nseg + 1);
+    const size_t head = ((out_bytes + 255) & ~(size_t)255) + ((off_bytes + 255) & ~(size_t)255);
     const size_t sb = sort_scratch_bytes(sp);
     keep_pool_memory();
     void* buf = nullptr;
     int rc;
-    if ((rc = dev_alloc_async(&buf, out_bytes + 256 + sb, s))) return rc;
+    if ((rc = dev_alloc_async(&buf, head + sb, s))) return rc;
     sp.out_hi = static_cast<uint64_t*>(buf);
     sp.out_lo = sp.out_hi + total;
     sp.out_ids = reinterpret_cast<uint32_t*>(sp.out_lo + total);
-    rc = sort_segments(sp, static_cast<char*>(buf) + ((out_bytes + 255) & ~(size_t)255), s);
+    uint64_t* off_dev = reinterpret_cast<uint64_t*>(static_cast<char*>(buf) +
+                                                    ((out_bytes + 255) & ~(size_t)255));
+    sp.seg_off_dev = off_dev;
+    rc = status_of(cudaMemcpyAsync(off_dev, seg_off_host, off_bytes, cudaMemcpyHostToDevice, s));
+    if (!rc) rc = sort_segments(sp, static_cast<char*>(buf) + head, s);
     if (!rc) rc = status_of(cudaMemcpyAsync(hi_dev, sp.out_hi, 8 * total, cudaMemcpyDeviceToDevice, s));
     if (!rc) rc = status_of(cudaMemcpyAsync(lo_dev, sp.out_lo, 8 * total, cudaMemcpyDeviceToDevice, s));
     if (!rc)
@@ -460,6 +481,8 @@ HC_API int hc_bruteforce(const void* db_dev, hc_dtype dtype, uint64_t n, uint32_
     return status_of(launch_bruteforce(db_dev, dtype, n, d, q_dev, nq, k, out_ids_dev, out_dist_dev,
                                        static_cast<cudaStream_t>(cuda_stream)));
 }
+
+HC_API uint64_t hc_launch_count(void) { return g_launches.load(); }
 
 HC_API void hc_debug_fail_alloc(long after) {
     g_alloc_count.store(0);

@@ -11,6 +11,9 @@
 
 namespace hc {
 
+// Every kernel launch the library issues is counted here (hc_launch_count).
+void count_launches(uint64_t n);
+
 // ------------------------------------------------------------ K1: keys
 // Keys of every row for every curve, written at the row's slot of each list
 // of its partition: list L = part*curves + c, slot list_off[L] + (r - start).
@@ -38,7 +41,8 @@ struct SortProblem {
     const uint64_t* hi;        // device, total records
     const uint64_t* lo;
     const uint32_t* ids;
-    std::vector<uint64_t> seg_off;  // host, nseg+1
+    std::vector<uint64_t> seg_off;  // host, nseg+1 (grid sizes)
+    const uint64_t* seg_off_dev;    // the same offsets on the device
     uint32_t key_bits;         // 1..128
     uint64_t* out_hi;          // device, total records (distinct from sources)
     uint64_t* out_lo;
@@ -48,6 +52,12 @@ struct SortProblem {
 size_t sort_scratch_bytes(const SortProblem& p);
 // Enqueues the whole sort on s using the given scratch (>= sort_scratch_bytes).
 int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s);
+
+// Small host tables written to device memory by a kernel that takes them
+// as a by-value parameter, so that no pageable copy (and its implicit
+// stream synchronisation) sits on the build path.
+constexpr uint32_t kMaxParamWords = 480;  // 8-byte words per launch (< 4 KB)
+cudaError_t upload_small(void* dst, const void* src, size_t bytes, cudaStream_t s);
 
 // ---------------------------------------------------- K3..K6: queries
 struct IndexView {

@@ -51,6 +51,7 @@ static unsigned grid_for(uint64_t work, unsigned threads) {
 cudaError_t launch_build_keys(const BuildKeysArgs& a, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     build_keys_kernel<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -59,6 +60,7 @@ cudaError_t launch_vector_keys(const void* x, uint64_t count, uint32_t row_bytes
     if (count == 0) return cudaSuccess;
     vector_keys_kernel<<<grid_for(count * P.curves, 256), 256, 0, s>>>(x, count, row_bytes, P, hi,
                                                                        lo);
+    count_launches(1);
     return cudaGetLastError();
 }
 

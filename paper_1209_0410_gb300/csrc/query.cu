@@ -277,6 +277,7 @@ struct QueryLaunch {
         const unsigned blocks = (a.nq + kQWarps - 1) / kQWarps;
         const size_t smem = sizeof(uint32_t) * kQWarps * a.ix.lists;
         query_kernel<F32, LPR, KR><<<blocks, kQWarps * 32, smem, s>>>(a);
+        count_launches(1);
         return cudaGetLastError();
     }
 };
@@ -288,6 +289,7 @@ struct BruteLaunch {
         const unsigned blocks = (nq + kQWarps - 1) / kQWarps;
         brute_kernel<F32, LPR, KR><<<blocks, kQWarps * 32, 0, s>>>(db, n, row_bytes, q, nq, k,
                                                                    ids, dist);
+        count_launches(1);
         return cudaGetLastError();
     }
 };
@@ -308,6 +310,7 @@ cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, in
     QueryArgs a{ix, q, nq, 1, 0, nullptr, nullptr, pos};
     const unsigned blocks = (nq + kQWarps - 1) / kQWarps;
     positions_kernel<<<blocks, kQWarps * 32, sizeof(uint32_t) * kQWarps * ix.lists, s>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 

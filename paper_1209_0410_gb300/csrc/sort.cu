@@ -17,6 +17,7 @@
 //           per warp round, a shared-memory reorder by digit, then coalesced
 //           runs to global memory.
 #include <algorithm>
+#include <cstring>
 
 #include "hc_internal.h"
 
@@ -38,11 +39,24 @@ struct SegInfo {
     uint32_t tile0;     // first global tile of the segment
 };
 
-__device__ __forceinline__ void tile_of(const uint32_t* tile_seg, const SegInfo* segs,
-                                        SegInfo& si, uint32_t& lt, uint64_t& start,
+// segment of global tile t: the last segment whose first tile is <= t
+// (segments without tiles share tile0 with the next one and are skipped)
+__device__ __forceinline__ uint32_t seg_of_tile(const SegInfo* segs, uint32_t nseg, uint32_t t) {
+    uint32_t lo = 0, hi = nseg;  // invariant: answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (segs[mid].tile0 <= t) lo = mid; else hi = mid;
+    }
+    while (segs[lo].ntiles == 0 || segs[lo].tile0 + segs[lo].ntiles <= t) ++lo;
+    return lo;
+}
+
+__device__ __forceinline__ void tile_of(uint32_t nseg, const SegInfo* segs, SegInfo& si,
+                                        uint32_t& seg, uint32_t& lt, uint64_t& start,
                                         uint32_t& count) {
     const uint32_t t = blockIdx.x;
-    si = segs[tile_seg[t]];
+    seg = seg_of_tile(segs, nseg, t);
+    si = segs[seg];
     lt = t - si.tile0;
     start = si.start + (uint64_t)lt * kTile;
     const uint64_t left = si.len - (uint64_t)lt * kTile;
@@ -76,15 +90,14 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 }
 
 __global__ void __launch_bounds__(kThreads) hist_kernel(const uint64_t* __restrict__ words,
-                                                        int shift,
-                                                        const uint32_t* __restrict__ tile_seg,
+                                                        int shift, uint32_t nseg,
                                                         const SegInfo* __restrict__ segs,
                                                         uint32_t* __restrict__ counts) {
     __shared__ uint32_t h[256];
     SegInfo si;
-    uint32_t lt, count;
+    uint32_t seg, lt, count;
     uint64_t start;
-    tile_of(tile_seg, segs, si, lt, start, count);
+    tile_of(nseg, segs, si, seg, lt, start, count);
     h[threadIdx.x] = 0;
     __syncthreads();
     const uint64_t* w = words + start;
@@ -119,9 +132,9 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const SegInfo* __restric
 
 __global__ void __launch_bounds__(kThreads) scatter_kernel(
     const uint64_t* __restrict__ wsrc, const uint32_t* __restrict__ psrc,
-    uint64_t* __restrict__ wdst, uint32_t* __restrict__ pdst, int shift,
-    const uint32_t* __restrict__ tile_seg, const SegInfo* __restrict__ segs,
-    const uint32_t* __restrict__ counts, const uint32_t* __restrict__ totals) {
+    uint64_t* __restrict__ wdst, uint32_t* __restrict__ pdst, int shift, uint32_t nseg,
+    const SegInfo* __restrict__ segs, const uint32_t* __restrict__ counts,
+    const uint32_t* __restrict__ totals) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* sw = reinterpret_cast<uint64_t*>(smem);            // kTile words
     uint32_t* sp = reinterpret_cast<uint32_t*>(sw + kTile);      // kTile positions
@@ -131,9 +144,9 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(
     __shared__ uint32_t warp_sums[kWarps];
 
     SegInfo si;
-    uint32_t lt, count;
+    uint32_t seg, lt, count;
     uint64_t start;
-    tile_of(tile_seg, segs, si, lt, start, count);
+    tile_of(nseg, segs, si, seg, lt, start, count);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
 
@@ -180,7 +193,6 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(
             run += c;
         }
         const uint32_t tile_start = block_exclusive_scan(run, warp_sums);
-        const uint32_t seg = __ldg(tile_seg + blockIdx.x);
         const uint32_t seg_prefix =
             block_exclusive_scan(__ldg(totals + (uint64_t)seg * 256 + dg), warp_sums);
         dstart[dg] = tile_start;
@@ -206,6 +218,25 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(
         const uint64_t g = gbase[(uint32_t)(v >> shift) & 0xFFu] + i;
         wdst[g] = v;
         pdst[g] = sp[i];
+    }
+}
+
+// the segment table from the device offsets (one thread: nseg is small)
+__global__ void seg_setup_kernel(const uint64_t* __restrict__ seg_off, uint32_t nseg,
+                                 SegInfo* __restrict__ segs) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t tiles = 0;
+    uint64_t cnt = 0;
+    for (uint32_t s = 0; s < nseg; ++s) {
+        SegInfo si;
+        si.start = seg_off[s];
+        si.len = seg_off[s + 1] - seg_off[s];
+        si.ntiles = (uint32_t)((si.len + kTile - 1) / kTile);
+        si.tile0 = tiles;
+        si.cnt_base = cnt;
+        cnt += 256ull * si.ntiles;
+        tiles += si.ntiles;
+        segs[s] = si;
     }
 }
 
@@ -237,28 +268,19 @@ struct Layout {
     uint64_t total = 0;
     uint32_t nseg = 0, ntiles = 0;
     uint64_t ncounts = 0;
-    std::vector<SegInfo> segs;
-    std::vector<uint32_t> tile_seg;
     size_t off_w = 0, off_pa = 0, off_pb = 0, off_counts = 0, off_totals = 0, off_segs = 0,
-           off_tiles = 0, bytes = 0;
+           bytes = 0;
 };
 
 Layout make_layout(const SortProblem& p) {
     Layout L;
     L.nseg = (uint32_t)(p.seg_off.size() - 1);
     L.total = p.seg_off.back();
-    L.segs.resize(L.nseg);
     for (uint32_t s = 0; s < L.nseg; ++s) {
-        SegInfo si;
-        si.start = p.seg_off[s];
-        si.len = p.seg_off[s + 1] - p.seg_off[s];
-        si.ntiles = (uint32_t)((si.len + kTile - 1) / kTile);
-        si.tile0 = L.ntiles;
-        si.cnt_base = L.ncounts;
-        L.ncounts += 256ull * si.ntiles;
-        L.ntiles += si.ntiles;
-        for (uint32_t t = 0; t < si.ntiles; ++t) L.tile_seg.push_back(s);
-        L.segs[s] = si;
+        const uint64_t len = p.seg_off[s + 1] - p.seg_off[s];
+        const uint32_t nt = (uint32_t)((len + kTile - 1) / kTile);
+        L.ncounts += 256ull * nt;
+        L.ntiles += nt;
     }
     size_t o = 0;
     L.off_w = o;       o = align_up(o + sizeof(uint64_t) * L.total);
@@ -267,7 +289,6 @@ Layout make_layout(const SortProblem& p) {
     L.off_counts = o;  o = align_up(o + sizeof(uint32_t) * (L.ncounts ? L.ncounts : 1));
     L.off_totals = o;  o = align_up(o + sizeof(uint32_t) * 256 * (L.nseg ? L.nseg : 1));
     L.off_segs = o;    o = align_up(o + sizeof(SegInfo) * (L.nseg ? L.nseg : 1));
-    L.off_tiles = o;   o = align_up(o + sizeof(uint32_t) * (L.ntiles ? L.ntiles : 1));
     L.bytes = o;
     return L;
 }
@@ -285,6 +306,36 @@ unsigned grid_stride_blocks(uint64_t work) {
 
 size_t sort_scratch_bytes(const SortProblem& p) { return make_layout(p).bytes; }
 
+namespace {
+struct SmallBlock {
+    uint64_t w[kMaxParamWords];
+};
+__global__ void upload_small_kernel(uint64_t* dst, SmallBlock b, uint32_t words) {
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = b.w[i];
+}
+}  // namespace
+
+cudaError_t upload_small(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    // dst is 8-byte aligned device memory of at least round_up(bytes, 8)
+    const uint8_t* p = static_cast<const uint8_t*>(src);
+    uint64_t* d = static_cast<uint64_t*>(dst);
+    while (bytes > 0) {
+        const size_t chunk = bytes < kMaxParamWords * 8 ? bytes : kMaxParamWords * 8;
+        SmallBlock b;
+        memset(&b, 0, sizeof(b));
+        memcpy(b.w, p, chunk);
+        const uint32_t words = (uint32_t)((chunk + 7) / 8);
+        upload_small_kernel<<<1, 128, 0, s>>>(d, b, words);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        p += chunk;
+        d += words;
+        bytes -= chunk;
+    }
+    return cudaSuccess;
+}
+
 int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     if (p.seg_off.size() < 2 || p.key_bits < 1 || p.key_bits > 128) return HC_ERR_ARG;
     Layout L = make_layout(p);
@@ -297,16 +348,11 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     uint32_t* counts = reinterpret_cast<uint32_t*>(base + L.off_counts);
     uint32_t* totals = reinterpret_cast<uint32_t*>(base + L.off_totals);
     SegInfo* segs = reinterpret_cast<SegInfo*>(base + L.off_segs);
-    uint32_t* tile_seg = reinterpret_cast<uint32_t*>(base + L.off_tiles);
 
     cudaError_t e;
-    e = cudaMemcpyAsync(segs, L.segs.data(), sizeof(SegInfo) * L.nseg, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return HC_ERR_CUDA;
-    if (L.ntiles) {
-        e = cudaMemcpyAsync(tile_seg, L.tile_seg.data(), sizeof(uint32_t) * L.ntiles,
-                            cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return HC_ERR_CUDA;
-    }
+    seg_setup_kernel<<<1, 32, 0, s>>>(p.seg_off_dev, L.nseg, segs);
+    count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
     const size_t dyn_smem = (sizeof(uint64_t) + sizeof(uint32_t)) * kTile;
     e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)dyn_smem);
@@ -329,12 +375,13 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     auto run_pass = [&](int digit) -> int {
         const int shift = (digit & 7) * 8;
         if (L.ntiles) {
-            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cur_w, shift, tile_seg, segs, counts);
+            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cur_w, shift, L.nseg, segs, counts);
             scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
             uint64_t* wd = wbuf[wnext];
             uint32_t* pd = pbuf[pnext];
             scatter_kernel<<<L.ntiles, kThreads, dyn_smem, s>>>(cur_w, cur_p, wd, pd, shift,
-                                                                tile_seg, segs, counts, totals);
+                                                                L.nseg, segs, counts, totals);
+            count_launches(3);
             if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
             cur_w = wd;
             cur_p = pd;
@@ -348,6 +395,7 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     {
         uint64_t* wd = wbuf[wnext];
         gather_words_kernel<<<grid_stride_blocks(L.total), 256, 0, s>>>(p.hi, cur_p, wd, L.total);
+        count_launches(1);
         if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
         cur_w = wd;
         wnext ^= 1;
@@ -357,6 +405,7 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     if (cur_w != p.out_hi) return HC_ERR_STATE;  // buffer bookkeeping broken
     gather_final_kernel<<<grid_stride_blocks(L.total), 256, 0, s>>>(p.lo, p.ids, cur_p, p.out_lo,
                                                                     p.out_ids, L.total);
+    count_launches(1);
     if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
     return HC_OK;
 }

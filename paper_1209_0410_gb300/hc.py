@@ -68,6 +68,8 @@ def lib():
         L.hc_sort_keys.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _vp]
         L.hc_query_positions.argtypes = [_vp, _vp, _u32, _vp, _vp]
         L.hc_bruteforce.argtypes = [_vp, ctypes.c_int, _u64, _u32, _vp, _u32, _u32, _vp, _vp, _vp]
+        L.hc_launch_count.argtypes = []
+        L.hc_launch_count.restype = ctypes.c_uint64
         L.hc_debug_fail_alloc.argtypes = [ctypes.c_long]
         L.hc_debug_fail_alloc.restype = None
         _LIB = L
@@ -286,6 +288,11 @@ def hc_bruteforce(db, q, k, stream=None):
                                    _dev(ids, "ids"), _dev(dist, "dist"), _stream(stream)),
                "hc_bruteforce")
     return ids, dist
+
+
+def hc_launch_count():
+    """Kernel launches issued by the library since it was loaded."""
+    return int(lib().hc_launch_count())
 
 
 def hc_debug_fail_alloc(after):
