@@ -199,6 +199,33 @@ HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
                         void* cuda_stream);
 
 /*
+ * hc_sort_keys_noalloc -- hc_sort_keys for callers that cannot let the
+ * library allocate device memory.  The paper has no counterpart: this entry
+ * point exists for deployment.  A process whose memory manager reserves the
+ * whole GPU up front (where a further cudaMalloc would fail or break its
+ * budget), or a latency-sensitive caller that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree, can sort with this call instead: it
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   Arguments and results are those of hc_sort_keys, with two limits:
+ *   seg_off_host[nseg] <= 262,144 records and nseg <= 256 segments; larger
+ *   problems return HC_ERR_ARG and touch nothing.
+ *   Scratch: a fixed 10 MiB device array inside libhc.so.  Every GPU on which
+ *   the library is loaded holds it until the process exits.  Every call uses
+ *   the same array and it keeps the last call's contents (the sort writes
+ *   everything it reads, so nothing has to be cleared first).  Calls that
+ *   overlap on the GPU (different streams, or different host threads on the
+ *   same device) race on that array and give wrong results: order them.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture begins.
+ *   Unlike hc_sort_keys, the call is asynchronous on cuda_stream: the sorted
+ *   arrays, and the scratch, are in use until the stream reaches it.
+ */
+HC_API int hc_sort_keys_noalloc(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
+                                const uint64_t* seg_off_host, uint32_t nseg, uint32_t key_bits,
+                                void* cuda_stream);
+
+/*
  * hc_query_positions -- the lower_bound step of Algorithm 2 alone: for each
  * query and list, the first entry whose key is >= the query's key.
  *   pos_dev   nq x lists int64

@@ -66,6 +66,7 @@ def lib():
         L.hc_hilbert_keys.argtypes = [_vp, ctypes.c_int, _u64, _u32, _u32, _u32, _vp, _vp, _vp,
                                       _vp]
         L.hc_sort_keys.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _vp]
+        L.hc_sort_keys_noalloc.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _vp]
         L.hc_query_positions.argtypes = [_vp, _vp, _u32, _vp, _vp]
         L.hc_bruteforce.argtypes = [_vp, ctypes.c_int, _u64, _u32, _vp, _u32, _u32, _vp, _vp, _vp]
         L.hc_launch_count.argtypes = []
@@ -265,6 +266,16 @@ def hc_sort_keys(hi, lo, ids, seg_off, key_bits=128, stream=None):
     _check(lib().hc_sort_keys(_dev(hi, "hi"), _dev(lo, "lo"), _dev(ids, "ids"),
                               off.ctypes.data_as(_vp), len(off) - 1, key_bits, _stream(stream)),
            "hc_sort_keys")
+
+
+def hc_sort_keys_noalloc(hi, lo, ids, seg_off, key_bits=128, stream=None):
+    """hc_sort_keys without any device allocation by the library (scratch is a
+    fixed array inside libhc.so; at most 262,144 records and 256 segments).
+    Asynchronous on the stream, unlike hc_sort_keys."""
+    off = np.ascontiguousarray(np.asarray(seg_off, dtype=np.uint64))
+    _check(lib().hc_sort_keys_noalloc(_dev(hi, "hi"), _dev(lo, "lo"), _dev(ids, "ids"),
+                                      off.ctypes.data_as(_vp), len(off) - 1, key_bits,
+                                      _stream(stream)), "hc_sort_keys_noalloc")
 
 
 def hc_query_positions(index, q, stream=None):
