@@ -122,7 +122,7 @@ def ncu_traffic(kernel_tag):
     if vals.get("source_sha") != source_sha(QUERY_SOURCES):
         return None, vals.get("source_sha")
     try:
-        return float(vals["dram_bytes_per_launch_scaled"]), vals.get("source_sha")
+        return float(vals["dram_bytes_per_launch"]), vals.get("source_sha")
     except (KeyError, ValueError):
         return None, vals.get("source_sha")
 
