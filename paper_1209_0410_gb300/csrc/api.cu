@@ -191,25 +191,35 @@ int build_index(hc_index* x, cudaStream_t s) {
     sp.seg_off = x->list_off;
     sp.seg_off_dev = x->list_off_dev;
     sp.key_bits = 8 * P.dims_per_curve;
+    sp.allow_sync = true;
     sp.out_hi = x->keys_hi;
     sp.out_lo = x->keys_lo;
     sp.out_ids = x->ids;
+    // ids are implied by the slot: list L holds its partition's rows in id
+    // order before the sort, so id = partition start + (slot - list start)
+    std::vector<uint64_t> id_base(x->lists);
+    for (uint32_t L = 0; L < x->lists; ++L)
+        id_base[L] = partition_start(L / P.curves, P.n, parts);
     const size_t sort_bytes = sort_scratch_bytes(sp);
-    const size_t key_bytes = (sizeof(uint64_t) * 2 + sizeof(uint32_t)) * total;
+    const size_t key_bytes = ((sizeof(uint64_t) * 2 * total) + 255) & ~(size_t)255;
+    const size_t base_bytes = (sizeof(uint64_t) * x->lists + 255) & ~(size_t)255;
     void* scratch = nullptr;
-    if ((rc = dev_alloc_async(&scratch, key_bytes + 256 + sort_bytes, s))) return rc;
+    if ((rc = dev_alloc_async(&scratch, key_bytes + base_bytes + sort_bytes, s))) return rc;
     uint64_t* hi0 = static_cast<uint64_t*>(scratch);
     uint64_t* lo0 = hi0 + total;
-    uint32_t* ids0 = reinterpret_cast<uint32_t*>(lo0 + total);
-    void* sort_scratch = static_cast<char*>(scratch) + ((key_bytes + 255) & ~(size_t)255);
+    uint64_t* id_base_dev = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + key_bytes);
+    void* sort_scratch = static_cast<char*>(scratch) + key_bytes + base_bytes;
 
     BuildKeysArgs ka{x->db, P.n, x->row_bytes, view_of(x).P, parts, x->list_off_dev, hi0, lo0,
-                     ids0};
+                     nullptr};
     rc = status_of(launch_build_keys(ka, s));
+    if (rc == HC_OK)
+        rc = status_of(upload_small(id_base_dev, id_base.data(), sizeof(uint64_t) * x->lists, s));
     if (rc == HC_OK) {
         sp.hi = hi0;
         sp.lo = lo0;
-        sp.ids = ids0;
+        sp.ids = nullptr;
+        sp.id_base_dev = id_base_dev;
         rc = sort_segments(sp, sort_scratch, s);
     }
     const int frc = status_of(cudaFreeAsync(scratch, s));
@@ -434,6 +444,7 @@ HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
     sp.ids = ids_dev;
     sp.seg_off.assign(seg_off_host, seg_off_host + nseg + 1);
     sp.key_bits = key_bits;
+    sp.allow_sync = true;   // this entry point synchronises anyway
     const size_t out_bytes = (sizeof(uint64_t) * 2 + sizeof(uint32_t)) * total;
     const size_t off_bytes = sizeof(uint64_t) * (nseg + 1);
     const size_t head = ((out_bytes + 255) & ~(size_t)255) + ((off_bytes + 255) & ~(size_t)255);

@@ -26,7 +26,7 @@ struct BuildKeysArgs {
     const uint64_t* list_off;  // device, lists+1
     uint64_t* hi;
     uint64_t* lo;
-    uint32_t* ids;
+    uint32_t* ids;             // may be null: ids are then implied by the slot
 };
 cudaError_t launch_build_keys(const BuildKeysArgs& a, cudaStream_t s);
 
@@ -44,6 +44,12 @@ struct SortProblem {
     std::vector<uint64_t> seg_off;  // host, nseg+1 (grid sizes)
     const uint64_t* seg_off_dev;    // the same offsets on the device
     uint32_t key_bits;         // 1..128
+    // May the sort synchronise the stream once (to learn whether a run of
+    // equal high words is too long for the high-word-first path)?  With
+    // false, every digit is sorted and nothing waits on the device.
+    bool allow_sync = false;
+    const uint64_t* id_base_dev = nullptr;  // device, nseg: ids[i] = id_base[s] + i - seg start
+                                            // (then `ids` is not read); null = gather ids
     uint64_t* out_hi;          // device, total records (distinct from sources)
     uint64_t* out_lo;
     uint32_t* out_ids;

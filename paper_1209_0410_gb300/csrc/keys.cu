@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
             const uint64_t g = a.list_off[part * a.P.curves + c] + local;
             a.hi[g] = hi;
             a.lo[g] = lo;
-            a.ids[g] = (uint32_t)r;
+            if (a.ids) a.ids[g] = (uint32_t)r;
         }
     }
 }

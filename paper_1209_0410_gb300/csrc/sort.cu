@@ -25,11 +25,15 @@ namespace hc {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;                 // histogram / scan / gather blocks
 constexpr int kWarps = kThreads / 32;
-constexpr int kIpt = 16;                       // records per thread
-constexpr int kTile = kThreads * kIpt;         // 4096 records per tile
-constexpr int kWarpItems = kTile / kWarps;     // 512 consecutive records per warp
+constexpr int kTile = 4096;                    // records per tile
+// scatter blocks: 16 warps of 256 consecutive records each (8 per lane), so
+// that the serial in-warp ranking chain is 8 rounds long
+constexpr int kSThreads = 512;
+constexpr int kSWarps = kSThreads / 32;
+constexpr int kIpt = kTile / kSThreads;        // 8 records per thread
+constexpr int kWarpItems = kTile / kSWarps;    // 256 consecutive records per warp
 
 struct SegInfo {
     uint64_t start;     // first record
@@ -37,6 +41,15 @@ struct SegInfo {
     uint64_t cnt_base;  // offset of the segment's counts block (256 x ntiles)
     uint32_t ntiles;
     uint32_t tile0;     // first global tile of the segment
+};
+
+// Final step: the low key words by the final positions, and the ids either by
+// the same gather or, when the ids are an affine function of the record
+// position (id = id_base[seg] + position - seg start, as hc_build lays them
+// out), computed without touching memory.
+struct FinalIds {
+    const uint32_t* ids;        // gathered when id_base is null
+    const uint64_t* id_base;    // device, one per segment, or null
 };
 
 // segment of global tile t: the last segment whose first tile is <= t
@@ -63,7 +76,8 @@ __device__ __forceinline__ void tile_of(uint32_t nseg, const SegInfo* segs, SegI
     count = (uint32_t)(left < (uint64_t)kTile ? left : (uint64_t)kTile);
 }
 
-// Exclusive scan of one value per thread over a 256-thread block.
+// Exclusive scan of one value per thread over a block of NW warps.
+template <int NW = kWarps>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
@@ -75,13 +89,13 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     if (lane == 31) warp_sums[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = lane < kWarps ? warp_sums[lane] : 0u;
+        uint32_t w = lane < NW ? warp_sums[lane] : 0u;
 #pragma unroll
-        for (int o = 1; o < kWarps; o <<= 1) {
+        for (int o = 1; o < NW; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
-        if (lane < kWarps) warp_sums[lane] = w;  // inclusive warp totals
+        if (lane < NW) warp_sums[lane] = w;  // inclusive warp totals
     }
     __syncthreads();
     const uint32_t before = warp ? warp_sums[warp - 1] : 0u;
@@ -130,18 +144,29 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const SegInfo* __restric
     }
 }
 
-__global__ void __launch_bounds__(kThreads) scatter_kernel(
+// Shared memory of one scatter tile: words and positions in sorted order, the
+// positions in input order, and per-warp digit counters (16-bit: a warp
+// ranks 512 records, a tile 4096).
+struct ScatterSmem {
+    uint64_t sw[kTile];
+    uint32_t sp[kTile];
+    uint32_t sp_in[kTile];
+    uint16_t whist[kSWarps][256];
+};
+
+// Two 512-thread blocks per SM: the words stay in registers (two per
+// record), the in-warp offsets are packed two per register, the positions
+// wait in shared memory.
+__global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
     const uint64_t* __restrict__ wsrc, const uint32_t* __restrict__ psrc,
     uint64_t* __restrict__ wdst, uint32_t* __restrict__ pdst, int shift, uint32_t nseg,
     const SegInfo* __restrict__ segs, const uint32_t* __restrict__ counts,
     const uint32_t* __restrict__ totals) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t* sw = reinterpret_cast<uint64_t*>(smem);            // kTile words
-    uint32_t* sp = reinterpret_cast<uint32_t*>(sw + kTile);      // kTile positions
-    __shared__ uint32_t whist[kWarps][256];
-    __shared__ uint32_t dstart[256];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
+    __shared__ uint16_t dstart[256];
     __shared__ uint64_t gbase[256];
-    __shared__ uint32_t warp_sums[kWarps];
+    __shared__ uint32_t warp_sums[kSWarps];
 
     SegInfo si;
     uint32_t seg, lt, count;
@@ -150,22 +175,21 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
 
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) whist[w][threadIdx.x] = 0;
+    for (int t = threadIdx.x; t < kSWarps * 256; t += kSThreads)
+        (&sm.whist[0][0])[t] = 0;
 
     uint64_t wv[kIpt];
-    uint32_t pv[kIpt];
-    uint32_t off[kIpt];
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
         const uint32_t i = warp * kWarpItems + j * 32 + lane;
         const bool valid = i < count;
         wv[j] = valid ? __ldg(wsrc + start + i) : 0ull;
-        pv[j] = valid ? (psrc ? __ldg(psrc + start + i) : (uint32_t)(start + i)) : 0u;
+        if (valid) sm.sp_in[i] = psrc ? __ldg(psrc + start + i) : (uint32_t)(start + i);
     }
     __syncthreads();
 
     // stable ranking inside the warp's 512 consecutive records, round by round
+    uint32_t offp[kIpt / 2];
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
         const uint32_t i = warp * kWarpItems + j * 32 + lane;
@@ -173,31 +197,41 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(
         const uint32_t dg = valid ? (uint32_t)(wv[j] >> shift) & 0xFFu : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, dg);
         const uint32_t rank = __popc(peers & lanemask_lt);
-        const uint32_t base = valid ? whist[warp][dg] : 0u;
+        const uint32_t base = valid ? sm.whist[warp][dg] : 0u;
         __syncwarp();
-        if (valid && rank == 0) whist[warp][dg] = base + __popc(peers);
+        if (valid && rank == 0) sm.whist[warp][dg] = (uint16_t)(base + __popc(peers));
         __syncwarp();
-        off[j] = base + rank;
+        const uint32_t off = base + rank;
+        if (j & 1)
+            offp[j >> 1] |= off << 16;
+        else
+            offp[j >> 1] = off;
     }
     __syncthreads();
 
     // per digit: offsets of each warp's run, the tile's digit starts, and the
     // global base of the digit's run for this tile
     {
+        // threads 0..255 own one digit each; the rest add zeros to the scans
         const uint32_t dg = threadIdx.x;
+        const bool own = dg < 256;
         uint32_t run = 0;
+        if (own) {
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = whist[w][dg];
-            whist[w][dg] = run;
-            run += c;
+            for (int w = 0; w < kSWarps; ++w) {
+                const uint32_t c = sm.whist[w][dg];
+                sm.whist[w][dg] = (uint16_t)run;
+                run += c;
+            }
         }
-        const uint32_t tile_start = block_exclusive_scan(run, warp_sums);
-        const uint32_t seg_prefix =
-            block_exclusive_scan(__ldg(totals + (uint64_t)seg * 256 + dg), warp_sums);
-        dstart[dg] = tile_start;
-        const uint32_t before = __ldg(counts + si.cnt_base + (uint64_t)dg * si.ntiles + lt);
-        gbase[dg] = si.start + seg_prefix + before - tile_start;
+        const uint32_t tile_start = block_exclusive_scan<kSWarps>(run, warp_sums);
+        const uint32_t seg_prefix = block_exclusive_scan<kSWarps>(
+            own ? __ldg(totals + (uint64_t)seg * 256 + dg) : 0u, warp_sums);
+        if (own) {
+            dstart[dg] = (uint16_t)tile_start;
+            const uint32_t before = __ldg(counts + si.cnt_base + (uint64_t)dg * si.ntiles + lt);
+            gbase[dg] = si.start + seg_prefix + before - tile_start;
+        }
     }
     __syncthreads();
 
@@ -206,18 +240,19 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(
         const uint32_t i = warp * kWarpItems + j * 32 + lane;
         if (i < count) {
             const uint32_t dg = (uint32_t)(wv[j] >> shift) & 0xFFu;
-            const uint32_t pos = dstart[dg] + whist[warp][dg] + off[j];
-            sw[pos] = wv[j];
-            sp[pos] = pv[j];
+            const uint32_t off = (offp[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
+            const uint32_t pos = (uint32_t)dstart[dg] + sm.whist[warp][dg] + off;
+            sm.sw[pos] = wv[j];
+            sm.sp[pos] = sm.sp_in[i];
         }
     }
     __syncthreads();
 
-    for (uint32_t i = threadIdx.x; i < count; i += kThreads) {
-        const uint64_t v = sw[i];
+    for (uint32_t i = threadIdx.x; i < count; i += kSThreads) {
+        const uint64_t v = sm.sw[i];
         const uint64_t g = gbase[(uint32_t)(v >> shift) & 0xFFu] + i;
         wdst[g] = v;
-        pdst[g] = sp[i];
+        pdst[g] = sm.sp[i];
     }
 }
 
@@ -250,26 +285,83 @@ __global__ void __launch_bounds__(256) gather_words_kernel(const uint64_t* __res
         dst[i] = __ldg(src + (pos ? __ldg(pos + i) : i));
 }
 
+// one tile per block, so the block knows its segment
 __global__ void __launch_bounds__(256) gather_final_kernel(
-    const uint64_t* __restrict__ lo, const uint32_t* __restrict__ ids,
-    const uint32_t* __restrict__ pos, uint64_t* __restrict__ out_lo,
-    uint32_t* __restrict__ out_ids, uint64_t total) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const uint32_t p = pos ? __ldg(pos + i) : (uint32_t)i;
-        out_lo[i] = __ldg(lo + p);
-        out_ids[i] = __ldg(ids + p);
+    const uint64_t* __restrict__ lo, FinalIds fid, const uint32_t* __restrict__ pos,
+    uint64_t* __restrict__ out_lo, uint32_t* __restrict__ out_ids, uint32_t nseg,
+    const SegInfo* __restrict__ segs) {
+    SegInfo si;
+    uint32_t seg, lt, count;
+    uint64_t start;
+    tile_of(nseg, segs, si, seg, lt, start, count);
+    const uint64_t base = fid.id_base ? __ldg(fid.id_base + seg) - si.start : 0;
+    for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
+        const uint32_t p = pos ? __ldg(pos + start + i) : (uint32_t)(start + i);
+        out_lo[start + i] = __ldg(lo + p);
+        out_ids[start + i] = fid.id_base ? (uint32_t)(base + p) : __ldg(fid.ids + p);
+    }
+}
+
+// Runs of records whose high words are equal must end ordered by (low word,
+// position); after sorting by the high word alone they are in position order.
+// One tile per block: a record outside any run is written in place; a record
+// in a run of at most kMaxRun finds the run's bounds, ranks itself among the
+// run's (low word, position) pairs and is written at run start + rank.  A
+// longer run sets *long_run, and the caller redoes the sort with every digit.
+constexpr uint32_t kMaxRun = 32;
+
+__global__ void __launch_bounds__(256) fixup_final_kernel(
+    const uint64_t* __restrict__ w, const uint32_t* __restrict__ pos,
+    const uint64_t* __restrict__ lo, FinalIds fid, uint64_t* __restrict__ out_lo,
+    uint32_t* __restrict__ out_ids, uint32_t nseg, const SegInfo* __restrict__ segs,
+    uint32_t* __restrict__ long_run) {
+    SegInfo si;
+    uint32_t seg, lt, count;
+    uint64_t start;
+    tile_of(nseg, segs, si, seg, lt, start, count);
+    const uint64_t id_base = fid.id_base ? __ldg(fid.id_base + seg) - si.start : 0;
+    const uint64_t seg_end = si.start + si.len;
+    for (uint32_t t = threadIdx.x; t < count; t += blockDim.x) {
+        const uint64_t i = start + t;
+        const uint64_t wi = __ldg(w + i);
+        const uint32_t pi = __ldg(pos + i);
+        const uint64_t li = __ldg(lo + pi);
+        const uint32_t idi = fid.id_base ? (uint32_t)(id_base + pi) : __ldg(fid.ids + pi);
+        const bool prev_eq = i > si.start && __ldg(w + i - 1) == wi;
+        const bool next_eq = i + 1 < seg_end && __ldg(w + i + 1) == wi;
+        uint64_t dst = i;
+        if (prev_eq || next_eq) {
+            uint64_t rs = i, re = i + 1;
+            while (rs > si.start && i - rs <= kMaxRun && __ldg(w + rs - 1) == wi) --rs;
+            while (re < seg_end && re - i <= kMaxRun && __ldg(w + re) == wi) ++re;
+            if (re - rs > kMaxRun) {
+                atomicOr(long_run, 1u);
+            } else {
+                uint32_t rank = 0;
+                for (uint64_t j = rs; j < re; ++j) {
+                    if (j == i) continue;
+                    const uint32_t pj = __ldg(pos + j);
+                    const uint64_t lj = __ldg(lo + pj);
+                    rank += (lj < li || (lj == li && pj < pi)) ? 1u : 0u;
+                }
+                dst = rs + rank;
+            }
+        }
+        out_lo[dst] = li;
+        out_ids[dst] = idi;
     }
 }
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+uint32_t* pbuf_of(uint32_t* a, uint32_t* b, int which) { return which ? b : a; }
 
 struct Layout {
     uint64_t total = 0;
     uint32_t nseg = 0, ntiles = 0;
     uint64_t ncounts = 0;
     size_t off_w = 0, off_pa = 0, off_pb = 0, off_counts = 0, off_totals = 0, off_segs = 0,
-           bytes = 0;
+           off_flag = 0, bytes = 0;
 };
 
 Layout make_layout(const SortProblem& p) {
@@ -289,6 +381,7 @@ Layout make_layout(const SortProblem& p) {
     L.off_counts = o;  o = align_up(o + sizeof(uint32_t) * (L.ncounts ? L.ncounts : 1));
     L.off_totals = o;  o = align_up(o + sizeof(uint32_t) * 256 * (L.nseg ? L.nseg : 1));
     L.off_segs = o;    o = align_up(o + sizeof(SegInfo) * (L.nseg ? L.nseg : 1));
+    L.off_flag = o;    o = align_up(o + sizeof(uint32_t));
     L.bytes = o;
     return L;
 }
@@ -353,7 +446,7 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     seg_setup_kernel<<<1, 32, 0, s>>>(p.seg_off_dev, L.nseg, segs);
     count_launches(1);
     if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
-    const size_t dyn_smem = (sizeof(uint64_t) + sizeof(uint32_t)) * kTile;
+    const size_t dyn_smem = sizeof(ScatterSmem);
     e = cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)dyn_smem);
     if (e != cudaSuccess) return HC_ERR_CUDA;
@@ -361,6 +454,46 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     const int digits = (int)((p.key_bits + 7) / 8);
     const int lo_passes = std::min(digits, 8);
     const int hi_passes = std::max(digits - 8, 0);
+    const dim3 scan_grid(256, L.nseg);
+    uint32_t* flag = reinterpret_cast<uint32_t*>(base + L.off_flag);
+
+    if (p.allow_sync && hi_passes > 0 && L.ntiles) {
+        // sort by the high word alone, then order runs of equal high words
+        uint64_t* wb[2] = {p.out_hi, wtmp};
+        int wn = (hi_passes % 2 == 1) ? 0 : 1;   // the last pass writes out_hi
+        int pn = 0;
+        const uint64_t* cw = p.hi;
+        const uint32_t* cp = nullptr;
+        for (int t = 8; t < 8 + hi_passes; ++t) {
+            const int shift = (t & 7) * 8;
+            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cw, shift, L.nseg, segs, counts);
+            scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
+            scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(cw, cp, wb[wn], pbuf_of(pa, pb, pn),
+                                                                 shift, L.nseg, segs, counts,
+                                                                 totals);
+            count_launches(3);
+            if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
+            cw = wb[wn];
+            cp = pbuf_of(pa, pb, pn);
+            wn ^= 1;
+            pn ^= 1;
+        }
+        if (cw != p.out_hi) return HC_ERR_STATE;
+        if (cudaMemsetAsync(flag, 0, sizeof(uint32_t), s) != cudaSuccess) return HC_ERR_CUDA;
+        fixup_final_kernel<<<L.ntiles, 256, 0, s>>>(p.out_hi, cp, p.lo,
+                                                     FinalIds{p.ids, p.id_base_dev}, p.out_lo,
+                                                     p.out_ids, L.nseg, segs, flag);
+        count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
+        uint32_t long_run = 1;
+        if (cudaMemcpyAsync(&long_run, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return HC_ERR_CUDA;
+        if (!long_run) return HC_OK;
+        // a run of equal high words longer than the fix-up handles: sort
+        // again with every digit (the sources are untouched)
+    }
     // word buffers written in sequence: each lo pass, the hi gather, each hi
     // pass; alternate so that the last write lands in out_hi.
     const int writes = lo_passes + 1 + hi_passes;
@@ -371,7 +504,6 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
 
     const uint64_t* cur_w = p.lo;
     const uint32_t* cur_p = nullptr;
-    const dim3 scan_grid(256, L.nseg);
     auto run_pass = [&](int digit) -> int {
         const int shift = (digit & 7) * 8;
         if (L.ntiles) {
@@ -379,7 +511,7 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
             uint64_t* wd = wbuf[wnext];
             uint32_t* pd = pbuf[pnext];
-            scatter_kernel<<<L.ntiles, kThreads, dyn_smem, s>>>(cur_w, cur_p, wd, pd, shift,
+            scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(cur_w, cur_p, wd, pd, shift,
                                                                 L.nseg, segs, counts, totals);
             count_launches(3);
             if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
@@ -403,8 +535,8 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     for (int t = 8; t < 8 + hi_passes; ++t)
         if (int rc = run_pass(t)) return rc;
     if (cur_w != p.out_hi) return HC_ERR_STATE;  // buffer bookkeeping broken
-    gather_final_kernel<<<grid_stride_blocks(L.total), 256, 0, s>>>(p.lo, p.ids, cur_p, p.out_lo,
-                                                                    p.out_ids, L.total);
+    gather_final_kernel<<<L.ntiles, 256, 0, s>>>(p.lo, FinalIds{p.ids, p.id_base_dev}, cur_p,
+                                                  p.out_lo, p.out_ids, L.nseg, segs);
     count_launches(1);
     if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
     return HC_OK;

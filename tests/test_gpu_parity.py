@@ -69,13 +69,20 @@ def test_hilbert_keys_bit_exact(hc, m, curves, mapped, dtype):
 
 
 # ------------------------------------------------------------------ K2
-@pytest.mark.parametrize("case", ["random", "duplicates", "narrow", "ragged", "reversed_ids"])
+SORT_CASES = ["random", "duplicates", "narrow", "ragged", "reversed_ids", "runs32", "runs33",
+              "hi_ties"]
+
+
+@pytest.mark.parametrize("case", SORT_CASES)
 def test_sort_keys_matches_stable_sort(hc, case):
+    """Both sort paths: the high-word-first path with its run fix-up (runs of
+    equal high words up to 32 long) and the every-digit path it falls back to."""
     import torch
-    rng = np.random.default_rng(["random", "duplicates", "narrow", "ragged", "reversed_ids"].index(case) + 1)
+    rng = np.random.default_rng(SORT_CASES.index(case) + 1)
     sizes = {"random": [30000], "duplicates": [20000, 5000], "narrow": [12289],
              "ragged": [0, 1, 4095, 4096, 4097, 9000, 33, 0, 2],
-             "reversed_ids": [8192, 7000]}[case]
+             "reversed_ids": [8192, 7000], "runs32": [32 * 700 + 5], "runs33": [33 * 300],
+             "hi_ties": [40000]}[case]
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     total = int(off[-1])
     key_bits = 128
@@ -92,6 +99,12 @@ def test_sort_keys_matches_stable_sort(hc, case):
         key_bits = 40
         hi[:] = 0
         lo &= np.uint64((1 << 40) - 1)
+    if case in ("runs32", "runs33"):
+        run = 32 if case == "runs32" else 33
+        hi = np.repeat(hi[: total // run + 1], run)[:total].copy()
+    if case == "hi_ties":          # short runs of equal high words, some equal keys
+        hi = hi[rng.integers(0, total // 3, size=total)].copy()
+        lo[rng.random(total) < 0.3] = np.uint64(5)
     ids = np.arange(total, dtype=np.uint32)
     if case == "reversed_ids":
         ids = ids[::-1].copy()
