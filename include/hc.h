@@ -139,6 +139,16 @@ HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, u
 HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids_host, void* out_dist_host, void* cuda_stream);
 
+/*
+ * hc_query_depths -- hc_query with one probe depth per query: p_dev holds nq
+ * uint32 depths (each 0..2^30) in device memory.  Used by the serving loop to
+ * mix requests of different depths in one launch and by the learned depth
+ * predictor.  No allocation; asynchronous on cuda_stream.
+ */
+HC_API int hc_query_depths(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k,
+                           const uint32_t* p_dev, int32_t* out_ids_dev, void* out_dist_dev,
+                           void* cuda_stream);
+
 /* hc_free -- releases an index and everything it owns (not db_dev).  The
  * caller makes sure no work using the index is still queued.  NULL is ok. */
 HC_API void hc_free(hc_index* idx);
@@ -241,6 +251,81 @@ HC_API int hc_query_positions(hc_index* idx, const void* q_dev, uint32_t nq, int
 HC_API int hc_bruteforce(const void* db_dev, hc_dtype dtype, uint64_t n, uint32_t d,
                          const void* q_dev, uint32_t nq, uint32_t k, int32_t* out_ids_dev,
                          void* out_dist_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------ serving */
+
+/*
+ * Online serving over resident indexes: continuous batching under an HBM
+ * budget.  The paper sends a GPU buffer of queued queries to the GPU when it
+ * is full or when the GPU is idle (Sec. 6, Algorithm 3, without its CPU
+ * branch here) and double-buffers the transfers (Sec. 5.2).  The server's
+ * dispatcher thread dispatches a batch when no batch is running, or when the
+ * queued queries fill a batch; up to `streams` batches run at once, so
+ * requests that arrive while others are on the GPU overlap with them.  The
+ * device state of every in-flight request (queries, depths, results) lives in
+ * an arena of exactly hbm_budget bytes allocated at creation: a request is
+ * admitted into a batch only when its state fits, and one that cannot fit even
+ * alone is refused at submission.  Each query is answered independently, so a
+ * request's result is the same alone and in any mix.  All calls are
+ * thread-safe.
+ */
+typedef struct hc_server hc_server;
+
+typedef struct {
+    uint32_t streams;            /* batches in flight at once, 1..16 (default 4) */
+    uint32_t max_batch_queries;  /* queries that fill a batch (default 16384) */
+    uint32_t default_p;          /* depth used for requests submitted with p = 0
+                                    (default 128) */
+} hc_serve_params;
+
+typedef struct {
+    uint64_t requests;           /* submitted */
+    uint64_t batches;            /* dispatched */
+    uint64_t batches_done;
+    uint64_t queries_done;
+    uint32_t max_inflight;       /* most batches seen on the GPU at once */
+    uint64_t arena_used;         /* bytes of the budget in use now */
+    uint64_t queued_queries;     /* waiting for admission now */
+} hc_serve_stats;
+
+/*
+ * hc_serve_create(_ex) -- starts a server over n_idx built indexes (borrowed:
+ * they must outlive the server).  hbm_budget >= 4096 bytes of device memory
+ * (plus the same of pinned host memory) are allocated now.  params may be
+ * NULL (defaults).  HC_ERR_OOM if the budget cannot be allocated.
+ */
+HC_API int hc_serve_create(hc_index* const* idx, uint32_t n_idx, uint64_t hbm_budget,
+                           hc_server** out);
+HC_API int hc_serve_create_ex(hc_index* const* idx, uint32_t n_idx, uint64_t hbm_budget,
+                              const hc_serve_params* params, hc_server** out);
+
+/*
+ * hc_serve_submit -- queues nq queries (HOST buffer, copied before return)
+ * against index index_id, k neighbours (1..128), depth p per side (0 = the
+ * server's depth predictor if one is attached, else params.default_p).
+ * *ticket identifies the request.  HC_ERR_BUDGET if the request's device
+ * state exceeds hbm_budget on its own.
+ */
+HC_API int hc_serve_submit(hc_server* srv, uint32_t index_id, const void* q_host, uint32_t nq,
+                           uint32_t k, uint32_t p, uint64_t* ticket);
+
+/*
+ * hc_serve_poll -- waits up to timeout_us (0 = just check) for a request.
+ * HC_OK: the nq x k ids (int32) and distances (int32 for uint8 indexes, float
+ * for float32) are copied to the HOST buffers and the ticket is released.
+ * HC_PENDING: not finished yet (the ticket stays valid).  HC_ERR_STATE:
+ * unknown or already collected ticket.  Other errors: the request failed (the
+ * ticket is released).
+ */
+HC_API int hc_serve_poll(hc_server* srv, uint64_t ticket, int32_t* ids_host, void* dist_host,
+                         uint32_t timeout_us);
+
+/* hc_serve_stats_get -- counters of the server (see hc_serve_stats). */
+HC_API int hc_serve_stats_get(hc_server* srv, hc_serve_stats* out);
+
+/* hc_serve_destroy -- finishes the queued and running requests, then frees
+ * the server (uncollected results are dropped).  NULL is ok. */
+HC_API void hc_serve_destroy(hc_server* srv);
 
 /* ------------------------------------------------------------ testing */
 

@@ -5,27 +5,10 @@
 #include <new>
 #include <vector>
 
-#include "hc_internal.h"
+#include "hc_index.h"
 
 using namespace hc;
 
-struct hc_index {
-    hc_build_params params{};
-    std::vector<uint32_t> dim_map;   // host copy, empty = consecutive
-    uint32_t* dim_map_dev = nullptr;
-    const void* db = nullptr;
-    void* db_owned = nullptr;
-    uint64_t* keys_hi = nullptr;
-    uint64_t* keys_lo = nullptr;
-    uint32_t* ids = nullptr;
-    uint64_t* list_off_dev = nullptr;
-    std::vector<uint64_t> list_off;
-    uint32_t lists = 0, row_bytes = 0;
-    // device staging of hc_query_host
-    void* st_q = nullptr;
-    void* st_out = nullptr;
-    size_t st_q_cap = 0, st_out_cap = 0;
-};
 
 static std::atomic<uint64_t> g_launches{0};
 
@@ -45,6 +28,12 @@ bool injected_failure() {
     if (after < 0) return false;
     return g_alloc_count.fetch_add(1) == after;
 }
+
+}  // namespace
+
+bool hc::alloc_should_fail() { return injected_failure(); }
+
+namespace {
 
 int status_of(cudaError_t e) {
     if (e == cudaSuccess) return HC_OK;
@@ -119,20 +108,6 @@ int check_params(const hc_build_params* p) {
     return HC_OK;
 }
 
-IndexView view_of(const hc_index* x) {
-    IndexView v;
-    v.db = x->db;
-    v.row_bytes = x->row_bytes;
-    v.d = x->params.d;
-    v.P = Projection{x->params.d, x->params.curves, x->params.dims_per_curve, x->dim_map_dev,
-                     x->params.dtype};
-    v.lists = x->lists;
-    v.list_off = x->list_off_dev;
-    v.keys_hi = x->keys_hi;
-    v.keys_lo = x->keys_lo;
-    v.ids = x->ids;
-    return v;
-}
 
 // The index arrays come from the stream-ordered pool; they are released in
 // order on the legacy default stream (after the work of every blocking
@@ -313,6 +288,19 @@ HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, u
         return HC_ERR_ARG;
     return status_of(launch_query(view_of(idx), q_dev, nq, k, p, out_ids_dev, out_dist_dev,
                                   static_cast<cudaStream_t>(cuda_stream)));
+}
+
+HC_API int hc_query_depths(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k,
+                           const uint32_t* p_dev, int32_t* out_ids_dev, void* out_dist_dev,
+                           void* cuda_stream) {
+    if (!idx || k < 1 || k > 128) return HC_ERR_ARG;
+    if (nq == 0) return HC_OK;
+    if (!q_dev || !p_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev)) return HC_ERR_ARG;
+    if (!is_device_ptr(q_dev) || !is_device_ptr(p_dev) || !is_device_ptr(out_ids_dev) ||
+        !is_device_ptr(out_dist_dev))
+        return HC_ERR_ARG;
+    return status_of(launch_query(view_of(idx), q_dev, nq, k, 0, out_ids_dev, out_dist_dev,
+                                  static_cast<cudaStream_t>(cuda_stream), p_dev));
 }
 
 HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,

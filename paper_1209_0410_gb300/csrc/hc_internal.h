@@ -14,6 +14,10 @@ namespace hc {
 // Every kernel launch the library issues is counted here (hc_launch_count).
 void count_launches(uint64_t n);
 
+// Host-side fault injection (hc_debug_fail_alloc): true when the library's
+// next allocation must report out-of-memory.
+bool alloc_should_fail();
+
 // ------------------------------------------------------------ K1: keys
 // Keys of every row for every curve, written at the row's slot of each list
 // of its partition: list L = part*curves + c, slot list_off[L] + (r - start).
@@ -78,8 +82,10 @@ struct IndexView {
     const uint32_t* ids;
 };
 
+// p_query (device, nq entries, nullable) gives each query its own depth.
 cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
-                         int32_t* out_ids, void* out_dist, cudaStream_t s);
+                         int32_t* out_ids, void* out_dist, cudaStream_t s,
+                         const uint32_t* p_query = nullptr);
 cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, int64_t* pos,
                              cudaStream_t s);
 cudaError_t launch_bruteforce(const void* db, hc_dtype dtype, uint64_t n, uint32_t d,

@@ -34,7 +34,8 @@ struct QueryArgs {
     uint32_t nq, k, p;
     int32_t* out_ids;
     void* out_dist;
-    int64_t* out_pos;   // positions-only kernel
+    int64_t* out_pos;            // positions-only kernel
+    const uint32_t* p_query;     // per-query depth (overrides p), or null
 };
 
 __device__ __forceinline__ uint4 ldg16(const void* p) {
@@ -184,14 +185,15 @@ __global__ void __launch_bounds__(kQWarps * 32) query_kernel(QueryArgs a) {
     const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
     const uint8_t* db = static_cast<const uint8_t*>(ix.db);
 
+    const uint32_t depth = a.p_query ? __ldg(a.p_query + qi) : a.p;
     WarpTopK<KR> top;
     top.init();
     for (uint32_t L = 0; L < ix.lists; ++L) {
         const uint64_t off = ix.list_off[L];
         const uint32_t n = (uint32_t)(ix.list_off[L + 1] - off);
         const uint32_t pos = pos_w[L];
-        const uint32_t lo = pos > a.p ? pos - a.p : 0u;
-        const uint32_t hi = (uint64_t)pos + a.p < (uint64_t)n ? pos + a.p : n;
+        const uint32_t lo = pos > depth ? pos - depth : 0u;
+        const uint32_t hi = (uint64_t)pos + depth < (uint64_t)n ? pos + depth : n;
         const uint32_t* idl = ix.ids + off;
         uint32_t next = lo + (uint32_t)lane < hi ? __ldg(idl + lo + lane) : 0u;
         for (uint32_t base = lo; base < hi; base += 32) {
@@ -297,9 +299,10 @@ struct BruteLaunch {
 }  // namespace
 
 cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
-                         int32_t* out_ids, void* out_dist, cudaStream_t s) {
+                         int32_t* out_ids, void* out_dist, cudaStream_t s,
+                         const uint32_t* p_query) {
     if (nq == 0) return cudaSuccess;
-    QueryArgs a{ix, q, nq, k, p, out_ids, out_dist, nullptr};
+    QueryArgs a{ix, q, nq, k, p, out_ids, out_dist, nullptr, p_query};
     return dispatch<QueryLaunch>(ix.P.dtype == HC_F32, lanes_per_row(ix.row_bytes), regs_for_k(k),
                                  a, s);
 }
@@ -307,7 +310,7 @@ cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32
 cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, int64_t* pos,
                              cudaStream_t s) {
     if (nq == 0) return cudaSuccess;
-    QueryArgs a{ix, q, nq, 1, 0, nullptr, nullptr, pos};
+    QueryArgs a{ix, q, nq, 1, 0, nullptr, nullptr, pos, nullptr};
     const unsigned blocks = (nq + kQWarps - 1) / kQWarps;
     positions_kernel<<<blocks, kQWarps * 32, sizeof(uint32_t) * kQWarps * ix.lists, s>>>(a);
     count_launches(1);

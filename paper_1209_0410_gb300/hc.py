@@ -41,6 +41,18 @@ class _IndexInfo(ctypes.Structure):
                 ("ids_dev", ctypes.c_void_p), ("db_dev", ctypes.c_void_p)]
 
 
+class _ServeParams(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32),
+                ("default_p", ctypes.c_uint32)]
+
+
+class _ServeStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("batches_done", ctypes.c_uint64), ("queries_done", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_uint32), ("arena_used", ctypes.c_uint64),
+                ("queued_queries", ctypes.c_uint64)]
+
+
 _LIB = None
 _vp = ctypes.c_void_p
 _u32, _u64, _i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
@@ -69,6 +81,16 @@ def lib():
         L.hc_sort_keys_noalloc.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _vp]
         L.hc_query_positions.argtypes = [_vp, _vp, _u32, _vp, _vp]
         L.hc_bruteforce.argtypes = [_vp, ctypes.c_int, _u64, _u32, _vp, _u32, _u32, _vp, _vp, _vp]
+        L.hc_query_depths.argtypes = [_vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]
+        L.hc_serve_create_ex.argtypes = [ctypes.POINTER(_vp), _u32, _u64,
+                                         ctypes.POINTER(_ServeParams), ctypes.POINTER(_vp)]
+        L.hc_serve_create.argtypes = [ctypes.POINTER(_vp), _u32, _u64, ctypes.POINTER(_vp)]
+        L.hc_serve_submit.argtypes = [_vp, _u32, _vp, _u32, _u32, _u32,
+                                      ctypes.POINTER(ctypes.c_uint64)]
+        L.hc_serve_poll.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _u32]
+        L.hc_serve_stats_get.argtypes = [_vp, ctypes.POINTER(_ServeStats)]
+        L.hc_serve_destroy.argtypes = [_vp]
+        L.hc_serve_destroy.restype = None
         L.hc_launch_count.argtypes = []
         L.hc_launch_count.restype = ctypes.c_uint64
         L.hc_debug_fail_alloc.argtypes = [ctypes.c_long]
@@ -193,6 +215,20 @@ def hc_query(index, q, k, p, out_ids=None, out_dist=None, stream=None):
     return out_ids, out_dist
 
 
+def hc_query_depths(index, q, k, p_per_query, out_ids=None, out_dist=None, stream=None):
+    """hc_query with one depth per query (a (nq,) int32/uint32 CUDA tensor)."""
+    nq = q.shape[0]
+    if out_ids is None:
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=_dist_dtype(index.dtype), device=q.device)
+    if nq:
+        _check(lib().hc_query_depths(index.handle, _dev(q, "q"), nq, k, _dev(p_per_query, "p"),
+                                     _dev(out_ids, "out_ids"), _dev(out_dist, "out_dist"),
+                                     _stream(stream)), "hc_query_depths")
+    return out_ids, out_dist
+
+
 def hc_query_host(index, q_host, k, p, out_ids=None, out_dist=None, stream=None):
     """hc_query from host buffers (numpy or CPU tensors, pinned or not)."""
     if isinstance(q_host, torch.Tensor):
@@ -308,3 +344,73 @@ def hc_launch_count():
 
 def hc_debug_fail_alloc(after):
     lib().hc_debug_fail_alloc(int(after))
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """An hc_server: continuous batching over resident indexes (see hc.h)."""
+
+    def __init__(self, indexes, hbm_budget, streams=4, max_batch_queries=16384, default_p=128):
+        self.indexes = list(indexes)      # keep them alive while serving
+        arr = (_vp * len(self.indexes))(*[ix.handle for ix in self.indexes])
+        prm = _ServeParams(streams, max_batch_queries, default_p)
+        h = ctypes.c_void_p()
+        _check(lib().hc_serve_create_ex(arr, len(self.indexes), hbm_budget, ctypes.byref(prm),
+                                        ctypes.byref(h)), "hc_serve_create")
+        self.handle = h
+        self._meta = {}
+
+    def submit(self, index_id, q, k, p):
+        """Queues a (nq, d) host array of queries; returns the ticket."""
+        q = np.ascontiguousarray(q)
+        t = ctypes.c_uint64()
+        _check(lib().hc_serve_submit(self.handle, index_id, q.ctypes.data_as(_vp), q.shape[0], k,
+                                     p, ctypes.byref(t)), "hc_serve_submit")
+        dt = np.float32 if self.indexes[index_id].dtype == HC_F32 else np.int32
+        self._meta[t.value] = (q.shape[0], k, dt)
+        return t.value
+
+    def poll(self, ticket, timeout_us=0):
+        """(ids, dist) numpy arrays when done, None while pending."""
+        nq, k, dt = self._meta[ticket]
+        ids = np.empty((nq, k), np.int32)
+        dist = np.empty((nq, k), dt)
+        rc = lib().hc_serve_poll(self.handle, ticket, ids.ctypes.data_as(_vp),
+                                 dist.ctypes.data_as(_vp), timeout_us)
+        if rc == HC_PENDING:
+            return None
+        del self._meta[ticket]
+        _check(rc, "hc_serve_poll")
+        return ids, dist
+
+    def stats(self):
+        st = _ServeStats()
+        _check(lib().hc_serve_stats_get(self.handle, ctypes.byref(st)), "hc_serve_stats_get")
+        return {f: getattr(st, f) for f, _ in _ServeStats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().hc_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hc_serve_create(indexes, hbm_budget, **params):
+    return Server(indexes, hbm_budget, **params)
+
+
+def hc_serve_submit(server, index_id, q_host, k, p):
+    return server.submit(index_id, q_host, k, p)
+
+
+def hc_serve_poll(server, ticket, timeout_us=0):
+    return server.poll(ticket, timeout_us)
+
+
+def hc_serve_destroy(server):
+    server.close()
