@@ -252,6 +252,82 @@ HC_API int hc_bruteforce(const void* db_dev, hc_dtype dtype, uint64_t n, uint32_
                          const void* q_dev, uint32_t nq, uint32_t k, int32_t* out_ids_dev,
                          void* out_dist_dev, void* cuda_stream);
 
+/* ------------------------------------------------- learned probe depth */
+
+/*
+ * Learned probe depth (not in the paper, which fixes one probe depth per
+ * subindex, Algorithm 2): a small MLP predicts from cheap per-query features
+ * the depth that reproduces the top-k of a large fixed depth.  The fixed-
+ * depth method stays the fallback and produces the training labels.
+ */
+typedef struct hc_mlp hc_mlp;
+
+/*
+ * hc_features -- 4 * curves float features per query (uint8 indexes with one
+ * partition, curves <= 16): for each curve c, with pos the lower_bound of the
+ * query key in list c,
+ *   [4c+0] oct(query key - key[pos-1]),  [4c+1] oct(key[pos] - query key),
+ *   [4c+2] oct(min distance), [4c+3] oct(floor(mean distance)) over the list
+ *   entries [pos-4, pos+4) clipped to the list;
+ * oct(0) = 0, oct(g) = 1 + e + f/65536 with e the top set bit of g and f the
+ * 16 bits below it; a missing neighbour or empty range gives 130.
+ *   feat_dev  nq x (4*curves) float.  Asynchronous; no allocation.
+ */
+HC_API int hc_features(hc_index* idx, const void* q_dev, uint32_t nq, float* feat_dev,
+                       void* cuda_stream);
+
+/*
+ * hc_probe_labels -- for each query, the minimal p in [0, p_max] whose top-k
+ * (ids) equals the top-k at p_max: a per-query binary search, valid because
+ * the windows and so the results are nested in p.  p_min_dev: nq uint32.
+ * Allocates scratch of about 12*k + 8 bytes per query on cuda_stream.
+ */
+HC_API int hc_probe_labels(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k,
+                           uint32_t p_max, uint32_t* p_min_dev, void* cuda_stream);
+
+/*
+ * hc_mlp_create -- an MLP in -> hidden1 -> hidden2 -> 1 (ReLU; each size
+ * 1..64), y = h2 . W3 + b3 after input normalisation (x - mu) * isd.  FP32
+ * parameters start at zero (set them with hc_mlp_set_params); Adam state is
+ * kept on the device.  max_batch bounds the training batch.
+ * Parameter layout (float): W1[in][h1], b1[h1], W2[h1][h2], b2[h2], W3[h2], b3.
+ */
+HC_API int hc_mlp_create(uint32_t in_dim, uint32_t hidden1, uint32_t hidden2, uint32_t max_batch,
+                         hc_mlp** out);
+HC_API uint32_t hc_mlp_param_count(const hc_mlp* mlp);
+/* host arrays: params (param_count floats), mu and isd (in_dim floats each);
+ * setting parameters resets the Adam state.  Both calls synchronise. */
+HC_API int hc_mlp_set_params(hc_mlp* mlp, const float* params_host, const float* mu_host,
+                             const float* isd_host);
+HC_API int hc_mlp_get_params(const hc_mlp* mlp, float* params_host, float* mu_host,
+                             float* isd_host);
+/*
+ * hc_mlp_gradients -- FP32 forward and backward of the mean squared error
+ * over n <= max_batch samples (x_dev: n x in, t_dev: n targets), gradients
+ * into grads_dev (param_count floats, nullable); loss_host (nullable) gets
+ * the loss and makes the call synchronous.
+ */
+HC_API int hc_mlp_gradients(hc_mlp* mlp, const float* x_dev, const float* t_dev, uint32_t n,
+                            float* grads_dev, float* loss_host, void* cuda_stream);
+/* hc_mlp_train_step -- one Adam step (beta 0.9 / 0.999, eps 1e-8) at
+ * learning rate lr on one batch; loss_host as above. */
+HC_API int hc_mlp_train_step(hc_mlp* mlp, const float* x_dev, const float* t_dev, uint32_t n,
+                             float lr, float* loss_host, void* cuda_stream);
+/* hc_mlp_forward -- y for n samples; bf16 = 0: FP32 throughout; bf16 = 1:
+ * inputs of every layer and weights rounded to bfloat16, FP32 accumulation
+ * (the inference arithmetic of hc_mlp_predict_depths). */
+HC_API int hc_mlp_forward(hc_mlp* mlp, const float* x_dev, uint32_t n, int bf16, float* y_dev,
+                          void* cuda_stream);
+/*
+ * hc_mlp_predict_depths -- fused features + BF16 inference: for every query
+ * p = clamp(ceil(2^(y + margin)), p_lo, p_hi) into p_dev (nq uint32), ready
+ * for hc_query_depths.  Requires in_dim = 4 * curves.
+ */
+HC_API int hc_mlp_predict_depths(hc_mlp* mlp, hc_index* idx, const void* q_dev, uint32_t nq,
+                                 float margin, uint32_t p_lo, uint32_t p_hi, uint32_t* p_dev,
+                                 void* cuda_stream);
+HC_API void hc_mlp_free(hc_mlp* mlp);
+
 /* ------------------------------------------------------------ serving */
 
 /*
@@ -319,6 +395,16 @@ HC_API int hc_serve_submit(hc_server* srv, uint32_t index_id, const void* q_host
  */
 HC_API int hc_serve_poll(hc_server* srv, uint64_t ticket, int32_t* ids_host, void* dist_host,
                          uint32_t timeout_us);
+
+/*
+ * hc_serve_attach_predictor -- requests on index_id submitted with p = 0 get
+ * a per-query depth from the learned predictor (hc_mlp_predict_depths with
+ * these margin / p_lo / p_hi) instead of params.default_p.  mlp is borrowed
+ * (outlives the server); NULL detaches.  The index must qualify for
+ * hc_features.
+ */
+HC_API int hc_serve_attach_predictor(hc_server* srv, uint32_t index_id, hc_mlp* mlp, float margin,
+                                     uint32_t p_lo, uint32_t p_hi);
 
 /* hc_serve_stats_get -- counters of the server (see hc_serve_stats). */
 HC_API int hc_serve_stats_get(hc_server* srv, hc_serve_stats* out);

@@ -612,3 +612,98 @@ int orc_quantize_batch(const float* x, uint64_t count, uint32_t* out) {
     for (uint64_t i = 0; i < count; ++i) out[i] = orc_quantize(x[i]);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Per-query features for the learned probe depth (not in the paper: the    */
+/* depth the paper fixes per subindex is predicted per query instead).      */
+/* ------------------------------------------------------------------------ */
+
+/* Octave encoding of a non-negative integer g (up to 128 bits): 0 for g = 0,
+ * else 1 + e + f/65536 with e the index of the top set bit and f the 16 bits
+ * below it (zero-filled).  Exact in float32 for every g < 2^128. */
+static double octave128(uint64_t hi, uint64_t lo) {
+    if (hi == 0 && lo == 0) return 0.0;
+    int e;
+    if (hi) {
+        e = 127;
+        while (!((hi >> (e - 64)) & 1ull)) --e;
+    } else {
+        e = 63;
+        while (!((lo >> e) & 1ull)) --e;
+    }
+    /* the 16 bits below bit e */
+    uint64_t f = 0;
+    for (int b = 1; b <= 16; ++b) {
+        int pos = e - b;
+        unsigned bit = 0;
+        if (pos >= 0) bit = pos >= 64 ? (unsigned)((hi >> (pos - 64)) & 1ull)
+                                      : (unsigned)((lo >> pos) & 1ull);
+        f = (f << 1) | bit;
+    }
+    return 1.0 + (double)e + (double)f / 65536.0;
+}
+
+/* (a - b) as 128-bit, a >= b */
+static void sub128(uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl, uint64_t* rh,
+                   uint64_t* rl) {
+    *rl = al - bl;
+    *rh = ah - bh - (al < bl ? 1u : 0u);
+}
+
+#define ORC_FEAT_NONE 130.0
+
+/*
+ * Features of nq uint8 queries on the first `curves` lists (partition 0):
+ * per curve c, with pos = lower_bound of the query key in list c:
+ *   [c*4+0] octave(query key - key[pos-1])          (NONE when pos = 0)
+ *   [c*4+1] octave(key[pos] - query key)            (NONE when pos = n)
+ *   [c*4+2] octave(min distance over entries [pos-4, pos+4) clipped)
+ *   [c*4+3] octave(floor(sum / count) of the same distances)  (NONE if empty)
+ * feat is nq x (4 * curves) float.
+ */
+int orc_features(const void* db, uint64_t n, uint32_t d, uint32_t curves, uint32_t m,
+                 const uint32_t* dim_map, const uint64_t* list_off, const uint64_t* keys_hi,
+                 const uint64_t* keys_lo, const uint32_t* ids, const void* queries, uint64_t nq,
+                 float* feat) {
+    orc_shape s = {ORC_U8, n, d, curves, m, dim_map, 1};
+    for (uint64_t qi = 0; qi < nq; ++qi) {
+        const void* q = row_ptr(&s, queries, qi);
+        for (uint32_t c = 0; c < curves; ++c) {
+            uint64_t off = list_off[c], len = list_off[c + 1] - off;
+            uint64_t kh, kl;
+            vector_key(&s, q, c, &kh, &kl);
+            uint64_t pos = lower_bound128(keys_hi + off, keys_lo + off, len, kh, kl);
+            double f0 = ORC_FEAT_NONE, f1 = ORC_FEAT_NONE, f2 = ORC_FEAT_NONE,
+                   f3 = ORC_FEAT_NONE;
+            uint64_t gh, gl;
+            if (pos > 0) {
+                sub128(kh, kl, keys_hi[off + pos - 1], keys_lo[off + pos - 1], &gh, &gl);
+                f0 = octave128(gh, gl);
+            }
+            if (pos < len) {
+                sub128(keys_hi[off + pos], keys_lo[off + pos], kh, kl, &gh, &gl);
+                f1 = octave128(gh, gl);
+            }
+            uint64_t lo = pos > 4 ? pos - 4 : 0, hi = pos + 4 < len ? pos + 4 : len;
+            if (hi > lo) {
+                int64_t mn = -1;
+                uint64_t sum = 0;
+                for (uint64_t i = lo; i < hi; ++i) {
+                    int64_t dd = (int64_t)sq_dist(&s, q, row_ptr(&s, db, ids[off + i]));
+                    if (mn < 0 || dd < mn) mn = dd;
+                    sum += (uint64_t)dd;
+                }
+                f2 = octave128(0, (uint64_t)mn);
+                f3 = octave128(0, sum / (hi - lo));
+            }
+            float* fo = feat + qi * 4 * curves + 4 * c;
+            fo[0] = (float)f0;
+            fo[1] = (float)f1;
+            fo[2] = (float)f2;
+            fo[3] = (float)f3;
+        }
+    }
+    return 0;
+}
+
+double orc_octave(uint64_t hi, uint64_t lo) { return octave128(hi, lo); }

@@ -60,6 +60,11 @@ def _lib():
         lib.orc_equiv_bound.restype = ctypes.c_double
         lib.orc_slack_depth.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double]
         lib.orc_slack_depth.restype = ctypes.c_uint32
+        lib.orc_features.argtypes = [_vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                     ctypes.c_uint32, _u32p, _u64p, _u64p, _u64p, _u32p, _vp,
+                                     ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]
+        lib.orc_octave.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.orc_octave.restype = ctypes.c_double
         _LIB = lib
     return _LIB
 
@@ -255,3 +260,53 @@ def recall_at(ids, dist, true_dist, k=10):
     ok = (dist[:, :k] <= kth) & (ids[:, :k] >= 0)
     hits = np.minimum(ok.sum(axis=1), k)
     return float(hits.mean() / k)
+
+
+# -------------------------------------------- learned probe depth features
+FEAT_NONE = 130.0
+
+
+def octave(g):
+    """Octave encoding of a non-negative integer below 2**128 (see hc_oracle.c)."""
+    g = int(g)
+    return _lib().orc_octave((g >> 64) & (2**64 - 1), g & (2**64 - 1))
+
+
+def features(index, db, queries):
+    """(nq, 4*curves) float32 features of uint8 queries (partition 0 lists)."""
+    db = np.ascontiguousarray(db)
+    queries = np.ascontiguousarray(queries, dtype=np.uint8)
+    if index.dtype != U8 or index.ell != 1:
+        raise ValueError("features are defined for uint8, single-partition indexes")
+    nq = queries.shape[0]
+    feat = np.zeros((nq, 4 * index.curves), np.float32)
+    dm_p = _ptr(index.dim_map, _u32p) if index.dim_map is not None else None
+    rc = _lib().orc_features(db.ctypes.data, index.n, index.d, index.curves, index.m, dm_p,
+                             _ptr(index.list_off, _u64p), _ptr(index.keys_hi, _u64p),
+                             _ptr(index.keys_lo, _u64p), _ptr(index.ids, _u32p),
+                             queries.ctypes.data, nq,
+                             feat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    if rc != 0:
+        raise ValueError("orc_features failed")
+    return feat
+
+
+def min_depth_labels(index, db, queries, k, p_max, nthreads=None):
+    """Minimal p in [0, p_max] whose top-k equals the top-k at p_max, by
+    direct search over p (valid because results are monotone in p)."""
+    ref_ids, _ = search(index, db, queries, k, p_max, nthreads)
+    nq = queries.shape[0]
+    lo = np.zeros(nq, np.int64)            # top-k(lo) may differ
+    hi = np.full(nq, p_max, np.int64)      # top-k(hi) equals the reference
+    while True:
+        active = lo < hi
+        if not active.any():
+            break
+        mid = (lo + hi) // 2
+        for p in np.unique(mid[active]):
+            sel = np.nonzero(active & (mid == p))[0]
+            ids, _ = search(index, db, queries[sel], k, int(p), nthreads)
+            same = (ids == ref_ids[sel]).all(axis=1)
+            hi[sel[same]] = p
+            lo[sel[~same]] = p + 1
+    return hi

@@ -42,3 +42,16 @@ inline IndexView view_of(const hc_index* x) {
 }
 
 }  // namespace hc
+
+struct hc_mlp;
+
+namespace hc {
+// The learned depth predictor (learned.cu): per-query depths into p_out.
+cudaError_t launch_predict_depths(hc_mlp* M, const hc_index* idx, const void* q, uint32_t nq,
+                                  float margin, uint32_t p_lo, uint32_t p_hi, uint32_t* p_out,
+                                  cudaStream_t s);
+// Makes the bf16 inference weights current and waits for them (call before
+// the model is used from several streams).
+// HC_ERR_ARG when the model's input size is not 4 * curves of the index.
+int mlp_prepare_inference(hc_mlp* M, const hc_index* idx, cudaStream_t s);
+}  // namespace hc

@@ -15,6 +15,7 @@
 //     even alone is refused at submission (HC_ERR_BUDGET).
 // Every query is answered independently by the query kernel (one warp per
 // query), so a request's result is the same alone and in any mix.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -104,8 +105,15 @@ struct Batch {
 
 }  // namespace
 
+struct Predictor {
+    hc_mlp* mlp = nullptr;
+    float margin = 0.f;
+    uint32_t p_lo = 1, p_hi = 512;
+};
+
 struct hc_server {
     std::vector<hc_index*> idx;
+    std::vector<Predictor> pred;
     uint64_t budget = 0;
     hc_serve_params params{};
     int device = 0;
@@ -172,6 +180,8 @@ Batch* form_batch(hc_server* S, int slot) {
         bytes = b2;
     }
     if (take.empty()) return nullptr;
+    // requests whose depth the predictor chooses go first (one contiguous range)
+    std::stable_partition(take.begin(), take.end(), [](const Request* r) { return r->p == 0; });
     Batch* b = new Batch();
     if (!S->arena->alloc(bytes, &b->off)) {
         delete b;
@@ -218,6 +228,16 @@ int launch_batch(hc_server* S, Batch* b) {
     const size_t in_bytes = b->ids_off - b->q_off;
     if (cudaMemcpyAsync(S->arena_dev + b->q_off, hq, in_bytes, cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
+        return HC_ERR_CUDA;
+    // learned depths for the leading p = 0 requests
+    const Predictor& pr = S->pred[b->index_id];
+    uint32_t n_auto = 0;
+    for (Request* r : b->reqs)
+        if (r->p == 0) n_auto += r->nq;
+    if (pr.mlp && n_auto &&
+        launch_predict_depths(pr.mlp, ix, S->arena_dev + b->q_off, n_auto, pr.margin, pr.p_lo,
+                              pr.p_hi, reinterpret_cast<uint32_t*>(S->arena_dev + b->p_off),
+                              st) != cudaSuccess)
         return HC_ERR_CUDA;
     if (launch_query(view_of(ix), S->arena_dev + b->q_off, b->nq, b->k, 0,
                      reinterpret_cast<int32_t*>(S->arena_dev + b->ids_off),
@@ -327,6 +347,7 @@ HC_API int hc_serve_create_ex(hc_index* const* idx, uint32_t n_idx, uint64_t hbm
     hc_server* S = new (std::nothrow) hc_server();
     if (!S) return HC_ERR_OOM;
     S->idx.assign(idx, idx + n_idx);
+    S->pred.assign(n_idx, Predictor());
     S->budget = hbm_budget;
     S->params = P;
     cudaGetDevice(&S->device);
@@ -413,6 +434,24 @@ HC_API int hc_serve_poll(hc_server* S, uint64_t ticket, int32_t* ids_host, void*
     S->live.erase(it);
     delete r;
     return status;
+}
+
+HC_API int hc_serve_attach_predictor(hc_server* S, uint32_t index_id, hc_mlp* mlp, float margin,
+                                     uint32_t p_lo, uint32_t p_hi) {
+    if (!S || index_id >= S->idx.size() || p_lo > p_hi || p_hi > (1u << 30)) return HC_ERR_ARG;
+    const hc_index* ix = S->idx[index_id];
+    if (mlp) {
+        if (ix->params.dtype != HC_U8 || ix->params.partitions != 1 || ix->params.curves > 16)
+            return HC_ERR_ARG;
+        if (int rc = mlp_prepare_inference(mlp, ix, S->streams[0])) return rc;
+    }
+    std::lock_guard<std::mutex> g(S->mu);
+    Predictor& p = S->pred[index_id];
+    p.mlp = mlp;
+    p.margin = margin;
+    p.p_lo = p_lo;
+    p.p_hi = p_hi;
+    return HC_OK;
 }
 
 HC_API int hc_serve_stats_get(hc_server* S, hc_serve_stats* out) {

@@ -91,6 +91,21 @@ def lib():
         L.hc_serve_stats_get.argtypes = [_vp, ctypes.POINTER(_ServeStats)]
         L.hc_serve_destroy.argtypes = [_vp]
         L.hc_serve_destroy.restype = None
+        L.hc_features.argtypes = [_vp, _vp, _u32, _vp, _vp]
+        L.hc_probe_labels.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp]
+        L.hc_mlp_create.argtypes = [_u32, _u32, _u32, _u32, ctypes.POINTER(_vp)]
+        L.hc_mlp_param_count.argtypes = [_vp]
+        L.hc_mlp_param_count.restype = ctypes.c_uint32
+        L.hc_mlp_set_params.argtypes = [_vp, _vp, _vp, _vp]
+        L.hc_mlp_get_params.argtypes = [_vp, _vp, _vp, _vp]
+        L.hc_mlp_gradients.argtypes = [_vp, _vp, _vp, _u32, _vp, _vp, _vp]
+        L.hc_mlp_train_step.argtypes = [_vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp]
+        L.hc_mlp_forward.argtypes = [_vp, _vp, _u32, ctypes.c_int, _vp, _vp]
+        L.hc_mlp_predict_depths.argtypes = [_vp, _vp, _vp, _u32, ctypes.c_float, _u32, _u32, _vp,
+                                            _vp]
+        L.hc_mlp_free.argtypes = [_vp]
+        L.hc_mlp_free.restype = None
+        L.hc_serve_attach_predictor.argtypes = [_vp, _u32, _vp, ctypes.c_float, _u32, _u32]
         L.hc_launch_count.argtypes = []
         L.hc_launch_count.restype = ctypes.c_uint64
         L.hc_debug_fail_alloc.argtypes = [ctypes.c_long]
@@ -383,6 +398,14 @@ class Server:
         _check(rc, "hc_serve_poll")
         return ids, dist
 
+    def attach_predictor(self, index_id, mlp, margin=0.0, p_lo=1, p_hi=512):
+        """Requests submitted with p = 0 get learned per-query depths."""
+        self._pred = getattr(self, "_pred", {})
+        self._pred[index_id] = mlp
+        _check(lib().hc_serve_attach_predictor(self.handle, index_id,
+                                               mlp.handle if mlp is not None else None, margin,
+                                               p_lo, p_hi), "hc_serve_attach_predictor")
+
     def stats(self):
         st = _ServeStats()
         _check(lib().hc_serve_stats_get(self.handle, ctypes.byref(st)), "hc_serve_stats_get")
@@ -414,3 +437,97 @@ def hc_serve_poll(server, ticket, timeout_us=0):
 
 def hc_serve_destroy(server):
     server.close()
+
+
+# ------------------------------------------------------ learned probe depth
+def hc_features(index, q, stream=None):
+    """(nq, 4*curves) float32 CUDA tensor of depth-predictor features."""
+    nq = q.shape[0]
+    feat = torch.empty((nq, 4 * index.curves), dtype=torch.float32, device=q.device)
+    if nq:
+        _check(lib().hc_features(index.handle, _dev(q, "q"), nq, _dev(feat, "feat"),
+                                 _stream(stream)), "hc_features")
+    return feat
+
+
+def hc_probe_labels(index, q, k, p_max, stream=None):
+    """(nq,) int32 CUDA tensor: minimal depth reproducing the top-k at p_max."""
+    nq = q.shape[0]
+    out = torch.empty(nq, dtype=torch.int32, device=q.device)
+    if nq:
+        _check(lib().hc_probe_labels(index.handle, _dev(q, "q"), nq, k, p_max, _dev(out, "out"),
+                                     _stream(stream)), "hc_probe_labels")
+    return out
+
+
+class MLP:
+    """hc_mlp: in -> h1 -> h2 -> 1 regressor with device-side Adam training."""
+
+    def __init__(self, n_in, h1=64, h2=64, max_batch=4096):
+        h = ctypes.c_void_p()
+        _check(lib().hc_mlp_create(n_in, h1, h2, max_batch, ctypes.byref(h)), "hc_mlp_create")
+        self.handle = h
+        self.n_in, self.h1, self.h2, self.max_batch = n_in, h1, h2, max_batch
+        self.nparam = int(lib().hc_mlp_param_count(h))
+
+    def set_params(self, theta, mu, isd):
+        t = np.ascontiguousarray(theta, np.float32)
+        m = np.ascontiguousarray(mu, np.float32)
+        i = np.ascontiguousarray(isd, np.float32)
+        assert t.size == self.nparam and m.size == self.n_in and i.size == self.n_in
+        _check(lib().hc_mlp_set_params(self.handle, t.ctypes.data_as(_vp), m.ctypes.data_as(_vp),
+                                       i.ctypes.data_as(_vp)), "hc_mlp_set_params")
+
+    def get_params(self):
+        t = np.empty(self.nparam, np.float32)
+        m = np.empty(self.n_in, np.float32)
+        i = np.empty(self.n_in, np.float32)
+        _check(lib().hc_mlp_get_params(self.handle, t.ctypes.data_as(_vp), m.ctypes.data_as(_vp),
+                                       i.ctypes.data_as(_vp)), "hc_mlp_get_params")
+        return t, m, i
+
+    def gradients(self, x, t, stream=None):
+        g = torch.empty(self.nparam, dtype=torch.float32, device=x.device)
+        loss = ctypes.c_float()
+        _check(lib().hc_mlp_gradients(self.handle, _dev(x, "x"), _dev(t, "t"), x.shape[0],
+                                      _dev(g, "g"), ctypes.byref(loss), _stream(stream)),
+               "hc_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, x, t, lr, want_loss=False, stream=None):
+        loss = ctypes.c_float()
+        _check(lib().hc_mlp_train_step(self.handle, _dev(x, "x"), _dev(t, "t"), x.shape[0], lr,
+                                       ctypes.byref(loss) if want_loss else None,
+                                       _stream(stream)), "hc_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def forward(self, x, bf16=False, stream=None):
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        if x.shape[0]:
+            _check(lib().hc_mlp_forward(self.handle, _dev(x, "x"), x.shape[0], 1 if bf16 else 0,
+                                        _dev(y, "y"), _stream(stream)), "hc_mlp_forward")
+        return y
+
+    def predict_depths(self, index, q, margin=0.0, p_lo=1, p_hi=512, stream=None):
+        nq = q.shape[0]
+        p = torch.empty(nq, dtype=torch.int32, device=q.device)
+        if nq:
+            _check(lib().hc_mlp_predict_depths(self.handle, index.handle, _dev(q, "q"), nq,
+                                               margin, p_lo, p_hi, _dev(p, "p"), _stream(stream)),
+                   "hc_mlp_predict_depths")
+        return p
+
+    def free(self):
+        if self.handle:
+            lib().hc_mlp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hc_mlp_create(n_in, h1=64, h2=64, max_batch=4096):
+    return MLP(n_in, h1, h2, max_batch)
