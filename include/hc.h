@@ -252,6 +252,52 @@ HC_API int hc_bruteforce(const void* db_dev, hc_dtype dtype, uint64_t n, uint32_
                          const void* q_dev, uint32_t nq, uint32_t k, int32_t* out_ids_dev,
                          void* out_dist_dev, void* cuda_stream);
 
+/* -------------------------------------------- many indexes, one launch */
+
+/*
+ * Batched uneven indexes: many hc_query calls (each an index with its own
+ * dtype, d, k, p and batch size) answered by one persistent kernel.  The
+ * queries are cut into tasks of (warps_per_block / warps_per_query) * tile
+ * queries, the tasks are ordered by their estimated bytes (largest first) and
+ * the kernel's blocks take them from an atomic counter.  warps_per_query
+ * warps share a query: each searches every warps_per_query-th list into its
+ * own top-k and the first folds the others' in (same results as hc_query).
+ */
+typedef struct {
+    hc_index* index;
+    const void* q_dev;           /* nq x d queries of the index's dtype */
+    uint32_t nq, k, p;           /* k 1..128, p 0..2^30 */
+    int32_t* out_ids_dev;        /* nq x k */
+    void* out_dist_dev;          /* nq x k int32 (HC_U8) or float (HC_F32) */
+    uint32_t warps_per_query;    /* 1, 2, 4 or 8 (0 = 1) */
+} hc_multi_job;
+
+typedef struct {
+    uint32_t warps_per_block;    /* 1..16, a power of two (default 8) */
+    uint32_t blocks_per_sm;      /* persistent blocks per SM (default 4) */
+    uint32_t tile;               /* query groups per task (default 2) */
+    uint32_t use_graph;          /* capture the launch in a CUDA graph */
+} hc_multi_config;
+
+typedef struct hc_multi_plan hc_multi_plan;
+
+/*
+ * hc_multi_plan_create -- validates the jobs, uploads the job and task
+ * tables and, with use_graph, captures the launch in a CUDA graph.  The
+ * plan refers to the jobs' buffers: new queries written into the same
+ * q_dev buffers are answered by the next hc_multi_run.  cfg may be NULL.
+ */
+HC_API int hc_multi_plan_create(const hc_multi_job* jobs, uint32_t njobs,
+                                const hc_multi_config* cfg, void* cuda_stream,
+                                hc_multi_plan** out);
+/* hc_multi_run -- one persistent launch (graph replay when captured). */
+HC_API int hc_multi_run(hc_multi_plan* plan, void* cuda_stream);
+HC_API void hc_multi_plan_free(hc_multi_plan* plan);
+/* hc_query_multi -- plan, run and free in one call (no graph); returns after
+ * the results are complete. */
+HC_API int hc_query_multi(const hc_multi_job* jobs, uint32_t njobs, const hc_multi_config* cfg,
+                          void* cuda_stream);
+
 /* ------------------------------------------------- learned probe depth */
 
 /*

@@ -61,45 +61,89 @@ __device__ __forceinline__ Acc reduce_scatter(Acc (&v)[LPR], uint32_t s) {
     return v[0];
 }
 
-// Distances of up to 32 rows (row r of the chunk has id shfl(id, r), valid
-// for r < cnt) to the query; returns this lane's packed candidate: the row
-// (lane % LPR) * (32 / LPR) + lane / LPR of the chunk, or kEmpty.
+// Candidates produced per lane by one 32-row chunk: rows wider than 8 lanes
+// are reduced 8 sub-batches at a time, leaving one candidate per group.
+template <int LPR>
+struct ChunkWidth {
+    static constexpr int G = LPR < 8 ? LPR : 8;   // sub-batches reduced together
+    static constexpr int NG = LPR / G;            // groups, candidates per lane
+};
+
+// Distances of up to 32 rows (row r of the chunk has id shfl(id, r), valid for
+// r < cnt) to the query.  LPR lanes read one row, 32 / LPR rows per warp
+// instruction, so the chunk takes LPR sub-batches; they are processed in
+// groups of G = min(LPR, 8): the G partial sums of a group are reduce-scattered
+// over the LPR lanes (G - 1 shuffles, then log2(LPR / G) plain ones), after
+// which lane s holds sub-batch s / (LPR / G) of the group.  out[g] is the
+// packed (distance, id) candidate of that row, or kEmpty (rows past cnt, and
+// the LPR / G - 1 lanes that hold a copy).
 template <bool F32, int LPR>
-__device__ __forceinline__ uint64_t chunk_candidates(const uint8_t* __restrict__ db,
-                                                     uint32_t row_bytes, const uint8_t* qrow,
-                                                     uint4 qv0, uint32_t id, uint32_t cnt,
-                                                     int lane) {
+__device__ __forceinline__ void chunk_candidates_n(const uint8_t* __restrict__ db,
+                                                   uint32_t row_bytes, const uint8_t* qrow,
+                                                   uint4 qv0, uint32_t id, uint32_t cnt, int lane,
+                                                   uint64_t (&out)[ChunkWidth<LPR>::NG]) {
     using Acc = typename std::conditional<F32, float, uint32_t>::type;
     constexpr int RPI = 32 / LPR;
-    constexpr int G = LPR < 8 ? LPR : 8;
+    constexpr int G = ChunkWidth<LPR>::G;
+    constexpr int NG = ChunkWidth<LPR>::NG;
+    constexpr int COPIES = LPR / G;
     const uint32_t s = (uint32_t)lane % LPR, g = (uint32_t)lane / LPR;
     const uint32_t vecs = row_bytes >> 4;
     const uint32_t vpl = (vecs + LPR - 1) / LPR;
-    Acc part[LPR];
 #pragma unroll
-    for (int j = 0; j < LPR; ++j) part[j] = Acc(0);
-    for (uint32_t v = 0; v < vpl; ++v) {
-        const uint32_t col = s + v * LPR;
-        const bool colok = col < vecs;
-        const uint4 qv = v == 0 ? qv0 : (colok ? ldg16(qrow + col * 16) : make_uint4(0, 0, 0, 0));
+    for (int gi = 0; gi < NG; ++gi) {
+        Acc part[G];
 #pragma unroll
-        for (int j0 = 0; j0 < LPR; j0 += G) {
+        for (int j = 0; j < G; ++j) part[j] = Acc(0);
+        for (uint32_t v = 0; v < vpl; ++v) {
+            const uint32_t col = s + v * LPR;
+            const bool colok = col < vecs;
+            const uint4 qv =
+                v == 0 ? qv0 : (colok ? ldg16(qrow + col * 16) : make_uint4(0, 0, 0, 0));
             uint4 rv[G];
 #pragma unroll
             for (int j = 0; j < G; ++j) {
-                const uint32_t r = (uint32_t)(j0 + j) * RPI + g;
+                const uint32_t r = (uint32_t)(gi * G + j) * RPI + g;
                 const uint32_t rid = __shfl_sync(0xffffffffu, id, (int)r);
                 rv[j] = (r < cnt && colok) ? ldg16(db + (size_t)rid * row_bytes + col * 16)
                                            : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
-            for (int j = 0; j < G; ++j) part[j0 + j] = acc_vec(rv[j], qv, part[j0 + j]);
+            for (int j = 0; j < G; ++j) part[j] = acc_vec(rv[j], qv, part[j]);
         }
+        // halving steps over the top log2(G) bits of s
+#pragma unroll
+        for (int w = LPR / 2, half = G / 2; half >= 1; w >>= 1, half >>= 1) {
+            const bool upper = (s & (uint32_t)w) != 0;
+#pragma unroll
+            for (int t = 0; t < half; ++t) {
+                const Acc send = upper ? part[t] : part[t + half];
+                const Acc keep = upper ? part[t + half] : part[t];
+                part[t] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+            }
+        }
+        // plain sums over the low log2(LPR / G) bits
+        Acc dsum = part[0];
+#pragma unroll
+        for (int w = COPIES / 2; w >= 1; w >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, w);
+        const uint32_t j = s / COPIES;
+        const uint32_t r = (uint32_t)(gi * G + j) * RPI + g;
+        const uint32_t cid = __shfl_sync(0xffffffffu, id, (int)(r < 32 ? r : 0));
+        out[gi] = (r < cnt && (s % COPIES) == 0) ? ((uint64_t)dist_bits(dsum) << 32) | cid : kEmpty;
     }
-    const Acc dsum = reduce_scatter<LPR>(part, s);
-    const uint32_t r = s * RPI + g;
-    const uint32_t cid = __shfl_sync(0xffffffffu, id, (int)r);
-    return r < cnt ? ((uint64_t)dist_bits(dsum) << 32) | cid : kEmpty;
+}
+
+// The single-candidate form (LPR <= 8): lane l holds row
+// (l % LPR) * (32 / LPR) + l / LPR of the chunk.
+template <bool F32, int LPR>
+__device__ __forceinline__ uint64_t chunk_candidates(const uint8_t* __restrict__ db,
+                                                     uint32_t row_bytes, const uint8_t* qrow,
+                                                     uint4 qv0, uint32_t id, uint32_t cnt,
+                                                     int lane) {
+    static_assert(LPR <= 8, "wider rows give several candidates per lane");
+    uint64_t out[1];
+    chunk_candidates_n<F32, LPR>(db, row_bytes, qrow, qv0, id, cnt, lane, out);
+    return out[0];
 }
 
 // first i in [0, n) with key[i] >= (kh, kl), else n
@@ -122,19 +166,22 @@ __device__ __forceinline__ uint32_t lower_bound_key(const uint64_t* __restrict__
     return first;
 }
 
-// K1 + K3 for one query: positions of the query key in every list, written
-// to pos_w[0..lists).
+// K1 + K3 for one query: positions of the query key in lists L0, L0 + Lstep,
+// ... written to pos_w[L].
 __device__ __forceinline__ void query_positions(const IndexView& ix, const uint8_t* qrow,
-                                                uint32_t* pos_w, int lane) {
+                                                uint32_t* pos_w, int lane, uint32_t L0 = 0,
+                                                uint32_t Lstep = 1) {
     const uint32_t curves = ix.P.curves;
     uint64_t khi = 0, klo = 0;
     if ((uint32_t)lane < curves) curve_key(qrow, ix.P, (uint32_t)lane, khi, klo);
-    for (uint32_t b = 0; b < ix.lists; b += 32) {
-        const uint32_t L = b + (uint32_t)lane;
+    const uint32_t mine = (ix.lists > L0) ? (ix.lists - L0 + Lstep - 1) / Lstep : 0;
+    for (uint32_t b = 0; b < mine; b += 32) {
+        const uint32_t t = b + (uint32_t)lane;
+        const uint32_t L = L0 + t * Lstep;
         const int c = (int)(L % curves);
         const uint64_t kh = __shfl_sync(0xffffffffu, khi, c);
         const uint64_t kl = __shfl_sync(0xffffffffu, klo, c);
-        if (L < ix.lists) {
+        if (t < mine) {
             const uint64_t off = ix.list_off[L];
             const uint32_t n = (uint32_t)(ix.list_off[L + 1] - off);
             pos_w[L] = lower_bound_key(ix.keys_hi + off, ix.keys_lo + off, n, kh, kl);
@@ -143,5 +190,37 @@ __device__ __forceinline__ void query_positions(const IndexView& ix, const uint8
     __syncwarp();
 }
 
+// Algorithm 2 for one query over the lists L0, L0 + Lstep, ... into the
+// warp's running top-k: keys, positions, then every window in 32-entry steps
+// (the next step's ids are loaded while the current rows are in flight).
+template <bool F32, int LPR, int KR>
+__device__ __forceinline__ void search_lists(const IndexView& ix, const uint8_t* qrow,
+                                             uint32_t depth, uint32_t k, uint32_t L0,
+                                             uint32_t Lstep, uint32_t* pos_w, WarpTopK<KR>& top,
+                                             int lane) {
+    query_positions(ix, qrow, pos_w, lane, L0, Lstep);
+    const uint32_t s = (uint32_t)lane % LPR;
+    const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
+    const uint8_t* db = static_cast<const uint8_t*>(ix.db);
+    for (uint32_t L = L0; L < ix.lists; L += Lstep) {
+        const uint64_t off = ix.list_off[L];
+        const uint32_t n = (uint32_t)(ix.list_off[L + 1] - off);
+        const uint32_t pos = pos_w[L];
+        const uint32_t lo = pos > depth ? pos - depth : 0u;
+        const uint32_t hi = (uint64_t)pos + depth < (uint64_t)n ? pos + depth : n;
+        const uint32_t* idl = ix.ids + off;
+        uint32_t next = lo + (uint32_t)lane < hi ? __ldg(idl + lo + lane) : 0u;
+        for (uint32_t base = lo; base < hi; base += 32) {
+            const uint32_t id = next;
+            const uint32_t cnt = min(32u, hi - base);
+            if (base + 32 < hi)
+                next = base + 32 + (uint32_t)lane < hi ? __ldg(idl + base + 32 + lane) : 0u;
+            uint64_t cand[ChunkWidth<LPR>::NG];
+            chunk_candidates_n<F32, LPR>(db, ix.row_bytes, qrow, qv0, id, cnt, lane, cand);
+#pragma unroll
+            for (int c = 0; c < ChunkWidth<LPR>::NG; ++c) top.offer(cand[c], k, lane);
+        }
+    }
+}
 
 }  // namespace hc

@@ -47,34 +47,10 @@ __global__ void __launch_bounds__(kQWarps * 32) query_kernel(QueryArgs a) {
     if (qi >= a.nq) return;
     const IndexView& ix = a.ix;
     const uint8_t* qrow = static_cast<const uint8_t*>(a.q) + (size_t)qi * ix.row_bytes;
-    uint32_t* pos_w = s_pos + warp * ix.lists;
-    query_positions(ix, qrow, pos_w, lane);
-
-    const uint32_t s = (uint32_t)lane % LPR;
-    const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
-    const uint8_t* db = static_cast<const uint8_t*>(ix.db);
-
     const uint32_t depth = a.p_query ? __ldg(a.p_query + qi) : a.p;
     WarpTopK<KR> top;
     top.init();
-    for (uint32_t L = 0; L < ix.lists; ++L) {
-        const uint64_t off = ix.list_off[L];
-        const uint32_t n = (uint32_t)(ix.list_off[L + 1] - off);
-        const uint32_t pos = pos_w[L];
-        const uint32_t lo = pos > depth ? pos - depth : 0u;
-        const uint32_t hi = (uint64_t)pos + depth < (uint64_t)n ? pos + depth : n;
-        const uint32_t* idl = ix.ids + off;
-        uint32_t next = lo + (uint32_t)lane < hi ? __ldg(idl + lo + lane) : 0u;
-        for (uint32_t base = lo; base < hi; base += 32) {
-            const uint32_t id = next;
-            const uint32_t cnt = min(32u, hi - base);
-            if (base + 32 < hi)
-                next = base + 32 + (uint32_t)lane < hi ? __ldg(idl + base + 32 + lane) : 0u;
-            const uint64_t cand =
-                chunk_candidates<F32, LPR>(db, ix.row_bytes, qrow, qv0, id, cnt, lane);
-            top.offer(cand, a.k, lane);
-        }
-    }
+    search_lists<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, top, lane);
     top.template store<F32>(a.k, lane, a.out_ids + (size_t)qi * a.k,
                             static_cast<uint32_t*>(a.out_dist) + (size_t)qi * a.k);
 }
@@ -110,8 +86,10 @@ __global__ void __launch_bounds__(kQWarps * 32) brute_kernel(const uint8_t* __re
     for (uint64_t base = 0; base < n; base += 32) {
         const uint32_t cnt = n - base < 32 ? (uint32_t)(n - base) : 32u;
         const uint32_t id = (uint32_t)(base + lane);
-        const uint64_t cand = chunk_candidates<F32, LPR>(db, row_bytes, qrow, qv0, id, cnt, lane);
-        top.offer(cand, k, lane);
+        uint64_t cand[ChunkWidth<LPR>::NG];
+        chunk_candidates_n<F32, LPR>(db, row_bytes, qrow, qv0, id, cnt, lane, cand);
+#pragma unroll
+        for (int c = 0; c < ChunkWidth<LPR>::NG; ++c) top.offer(cand[c], k, lane);
     }
     top.template store<F32>(k, lane, out_ids + (size_t)qi * k,
                             static_cast<uint32_t*>(out_dist) + (size_t)qi * k);

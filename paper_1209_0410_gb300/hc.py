@@ -53,6 +53,17 @@ class _ServeStats(ctypes.Structure):
                 ("queued_queries", ctypes.c_uint64)]
 
 
+class _MultiJob(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_void_p), ("q_dev", ctypes.c_void_p), ("nq", ctypes.c_uint32),
+                ("k", ctypes.c_uint32), ("p", ctypes.c_uint32), ("out_ids_dev", ctypes.c_void_p),
+                ("out_dist_dev", ctypes.c_void_p), ("warps_per_query", ctypes.c_uint32)]
+
+
+class _MultiConfig(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("tile", ctypes.c_uint32), ("use_graph", ctypes.c_uint32)]
+
+
 _LIB = None
 _vp = ctypes.c_void_p
 _u32, _u64, _i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
@@ -106,6 +117,13 @@ def lib():
         L.hc_mlp_free.argtypes = [_vp]
         L.hc_mlp_free.restype = None
         L.hc_serve_attach_predictor.argtypes = [_vp, _u32, _vp, ctypes.c_float, _u32, _u32]
+        L.hc_multi_plan_create.argtypes = [ctypes.POINTER(_MultiJob), _u32,
+                                           ctypes.POINTER(_MultiConfig), _vp, ctypes.POINTER(_vp)]
+        L.hc_multi_run.argtypes = [_vp, _vp]
+        L.hc_multi_plan_free.argtypes = [_vp]
+        L.hc_multi_plan_free.restype = None
+        L.hc_query_multi.argtypes = [ctypes.POINTER(_MultiJob), _u32, ctypes.POINTER(_MultiConfig),
+                                     _vp]
         L.hc_launch_count.argtypes = []
         L.hc_launch_count.restype = ctypes.c_uint64
         L.hc_debug_fail_alloc.argtypes = [ctypes.c_long]
@@ -531,3 +549,66 @@ class MLP:
 
 def hc_mlp_create(n_in, h1=64, h2=64, max_batch=4096):
     return MLP(n_in, h1, h2, max_batch)
+
+
+# ---------------------------------------------- many indexes, one launch
+class MultiJob:
+    """One hc_query inside a persistent multi-index launch; owns its outputs."""
+
+    def __init__(self, index, q, k, p, warps_per_query=1):
+        self.index, self.q, self.k, self.p = index, q, k, p
+        self.warps_per_query = warps_per_query
+        nq = q.shape[0]
+        self.ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        self.dist = torch.empty((nq, k), dtype=_dist_dtype(index.dtype), device=q.device)
+
+    def _c(self):
+        nq = self.q.shape[0]
+        return _MultiJob(self.index.handle.value, self.q.data_ptr() if nq else 0, nq, self.k,
+                         self.p, self.ids.data_ptr() if nq else 0,
+                         self.dist.data_ptr() if nq else 0, self.warps_per_query)
+
+
+def _multi_arrays(jobs, config):
+    arr = (_MultiJob * len(jobs))(*[j._c() for j in jobs])
+    cfg = None
+    if config is not None:
+        cfg = _MultiConfig(config.get("warps_per_block", 8), config.get("blocks_per_sm", 4),
+                           config.get("tile", 2), 1 if config.get("use_graph", True) else 0)
+    return arr, cfg
+
+
+class MultiPlan:
+    """hc_multi_plan: a persistent launch over many jobs, optionally a CUDA graph."""
+
+    def __init__(self, jobs, config=None, stream=None):
+        self.jobs = list(jobs)
+        arr, cfg = _multi_arrays(self.jobs, config)
+        h = ctypes.c_void_p()
+        _check(lib().hc_multi_plan_create(arr, len(self.jobs),
+                                          ctypes.byref(cfg) if cfg is not None else None,
+                                          _stream(stream), ctypes.byref(h)),
+               "hc_multi_plan_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(lib().hc_multi_run(self.handle, _stream(stream)), "hc_multi_run")
+
+    def free(self):
+        if self.handle:
+            lib().hc_multi_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hc_query_multi(jobs, config=None, stream=None):
+    """Answers every job in one persistent launch (no graph); returns when done."""
+    arr, cfg = _multi_arrays(jobs, config)
+    _check(lib().hc_query_multi(arr, len(jobs), ctypes.byref(cfg) if cfg is not None else None,
+                                _stream(stream)), "hc_query_multi")
+    return jobs
