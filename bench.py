@@ -51,6 +51,16 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hc", "reference"], default="hc")
+    ap.add_argument("--workload", choices=["scale", "uneven", "learned", "serve"],
+                    default="scale",
+                    help="scale: the headline (build + query at N=10M); uneven: 64 indexes in "
+                         "one persistent launch; learned: learned probe depth; serve: online "
+                         "serving under fluctuating load")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-n", type=int, default=50_000_000)
+    ap.add_argument("--train-queries", type=int, default=1_000_000)
+    ap.add_argument("--heldout-queries", type=int, default=100_000)
+    ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache path")
     ap.add_argument("--n-db", type=int, default=10_000_000)
     ap.add_argument("--nq", type=int, default=100_000)
     ap.add_argument("--p", type=int, default=128)
@@ -425,6 +435,15 @@ def main():
     a = parse_args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "uneven":
+        from bench_workloads import run_uneven
+        return run_uneven(a)
+    if a.workload == "learned":
+        from bench_workloads import run_learned
+        return run_learned(a)
+    if a.workload == "serve":
+        from bench_workloads import run_serve
+        return run_serve(a)
     return run_hc(a)
 
 

@@ -442,6 +442,12 @@ HC_API int hc_serve_submit(hc_server* srv, uint32_t index_id, const void* q_host
 HC_API int hc_serve_poll(hc_server* srv, uint64_t ticket, int32_t* ids_host, void* dist_host,
                          uint32_t timeout_us);
 
+/* hc_serve_poll_ex -- hc_serve_poll that also reports, on completion, the
+ * request's latency in nanoseconds: from its submission to its results
+ * being ready in host memory (latency_ns nullable). */
+HC_API int hc_serve_poll_ex(hc_server* srv, uint64_t ticket, int32_t* ids_host, void* dist_host,
+                            uint32_t timeout_us, uint64_t* latency_ns);
+
 /*
  * hc_serve_attach_predictor -- requests on index_id submitted with p = 0 get
  * a per-query depth from the learned predictor (hc_mlp_predict_depths with

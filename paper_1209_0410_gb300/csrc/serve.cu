@@ -76,7 +76,14 @@ class Arena {
     size_t used_ = 0;
 };
 
+uint64_t now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
 struct Request {
+    uint64_t t_submit = 0, t_done = 0;   // steady-clock ns
     uint64_t ticket = 0;
     uint32_t index_id = 0, nq = 0, k = 0, p = 0;
     std::vector<uint8_t> q;
@@ -151,7 +158,11 @@ void finalize(hc_server* S, Batch* b, int status) {
             row += r->nq;
         }
     }
-    for (Request* r : b->reqs) r->status = status;
+    const uint64_t t = now_ns();
+    for (Request* r : b->reqs) {
+        r->status = status;
+        r->t_done = t;
+    }
     S->arena->release(b->off, b->bytes);
     S->slot_busy[b->slot] = false;
     S->stats.queries_done += b->nq;
@@ -397,6 +408,7 @@ HC_API int hc_serve_submit(hc_server* S, uint32_t index_id, const void* q_host, 
     r->p = p;
     r->q.assign(static_cast<const uint8_t*>(q_host),
                 static_cast<const uint8_t*>(q_host) + (size_t)nq * rb);
+    r->t_submit = now_ns();
     {
         std::lock_guard<std::mutex> g(S->mu);
         if (S->stop) {
@@ -414,26 +426,37 @@ HC_API int hc_serve_submit(hc_server* S, uint32_t index_id, const void* q_host, 
     return HC_OK;
 }
 
+HC_API int hc_serve_poll_ex(hc_server* S, uint64_t ticket, int32_t* ids_host, void* dist_host,
+                            uint32_t timeout_us, uint64_t* latency_ns) {
+    if (!S) return HC_ERR_ARG;
+    uint64_t lat = 0;
+    int rc;
+    {
+        std::unique_lock<std::mutex> lock(S->mu);
+        auto it = S->live.find(ticket);
+        if (it == S->live.end()) return HC_ERR_STATE;
+        Request* r = it->second;
+        if (r->status == HC_PENDING && timeout_us > 0)
+            S->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us),
+                                [&] { return r->status != HC_PENDING; });
+        if (r->status == HC_PENDING) return HC_PENDING;
+        rc = r->status;
+        lat = r->t_done - r->t_submit;
+        if (rc == HC_OK) {
+            if (!ids_host || !dist_host) return HC_ERR_ARG;
+            std::memcpy(ids_host, r->ids.data(), r->ids.size() * sizeof(int32_t));
+            std::memcpy(dist_host, r->dist.data(), r->dist.size() * sizeof(uint32_t));
+        }
+        S->live.erase(it);
+        delete r;
+    }
+    if (latency_ns) *latency_ns = lat;
+    return rc;
+}
+
 HC_API int hc_serve_poll(hc_server* S, uint64_t ticket, int32_t* ids_host, void* dist_host,
                          uint32_t timeout_us) {
-    if (!S) return HC_ERR_ARG;
-    std::unique_lock<std::mutex> lock(S->mu);
-    auto it = S->live.find(ticket);
-    if (it == S->live.end()) return HC_ERR_STATE;
-    Request* r = it->second;
-    if (r->status == HC_PENDING && timeout_us > 0)
-        S->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us),
-                            [&] { return r->status != HC_PENDING; });
-    if (r->status == HC_PENDING) return HC_PENDING;
-    const int status = r->status;
-    if (status == HC_OK) {
-        if (!ids_host || !dist_host) return HC_ERR_ARG;
-        std::memcpy(ids_host, r->ids.data(), r->ids.size() * sizeof(int32_t));
-        std::memcpy(dist_host, r->dist.data(), r->dist.size() * sizeof(uint32_t));
-    }
-    S->live.erase(it);
-    delete r;
-    return status;
+    return hc_serve_poll_ex(S, ticket, ids_host, dist_host, timeout_us, nullptr);
 }
 
 HC_API int hc_serve_attach_predictor(hc_server* S, uint32_t index_id, hc_mlp* mlp, float margin,

@@ -100,6 +100,8 @@ def lib():
                                       ctypes.POINTER(ctypes.c_uint64)]
         L.hc_serve_poll.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _u32]
         L.hc_serve_stats_get.argtypes = [_vp, ctypes.POINTER(_ServeStats)]
+        L.hc_serve_poll_ex.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _u32,
+                                       ctypes.POINTER(ctypes.c_uint64)]
         L.hc_serve_destroy.argtypes = [_vp]
         L.hc_serve_destroy.restype = None
         L.hc_features.argtypes = [_vp, _vp, _u32, _vp, _vp]
@@ -403,17 +405,21 @@ class Server:
         self._meta[t.value] = (q.shape[0], k, dt)
         return t.value
 
-    def poll(self, ticket, timeout_us=0):
-        """(ids, dist) numpy arrays when done, None while pending."""
+    def poll(self, ticket, timeout_us=0, with_latency=False):
+        """(ids, dist) numpy arrays when done (plus the latency in seconds
+        with with_latency), None while pending."""
         nq, k, dt = self._meta[ticket]
         ids = np.empty((nq, k), np.int32)
         dist = np.empty((nq, k), dt)
-        rc = lib().hc_serve_poll(self.handle, ticket, ids.ctypes.data_as(_vp),
-                                 dist.ctypes.data_as(_vp), timeout_us)
+        lat = ctypes.c_uint64()
+        rc = lib().hc_serve_poll_ex(self.handle, ticket, ids.ctypes.data_as(_vp),
+                                    dist.ctypes.data_as(_vp), timeout_us, ctypes.byref(lat))
         if rc == HC_PENDING:
             return None
         del self._meta[ticket]
         _check(rc, "hc_serve_poll")
+        if with_latency:
+            return ids, dist, lat.value * 1e-9
         return ids, dist
 
     def attach_predictor(self, index_id, mlp, margin=0.0, p_lo=1, p_hi=512):
