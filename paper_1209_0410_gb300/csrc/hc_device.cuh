@@ -97,6 +97,77 @@ __device__ __forceinline__ void hilbert_key(uint32_t (&X)[16], uint64_t& hi, uin
     }
 }
 
+// 4x4 byte transpose: out[b] byte k = in[k] byte b.
+__device__ __forceinline__ void transpose4x4_bytes(uint32_t a0, uint32_t a1, uint32_t a2,
+                                                   uint32_t a3, uint32_t (&out)[4]) {
+    const uint32_t t0 = __byte_perm(a0, a1, 0x5140), t1 = __byte_perm(a0, a1, 0x7362);
+    const uint32_t t2 = __byte_perm(a2, a3, 0x5140), t3 = __byte_perm(a2, a3, 0x7362);
+    out[0] = __byte_perm(t0, t2, 0x5410);
+    out[1] = __byte_perm(t0, t2, 0x7632);
+    out[2] = __byte_perm(t1, t3, 0x5410);
+    out[3] = __byte_perm(t1, t3, 0x7632);
+}
+
+// Four 16-coordinate Hilbert keys at once, SIMD within a register: byte k of
+// X[i] is coordinate i of key k, and every step of hilbert_key<16> becomes
+// byte-parallel logic (per-byte masks from a multiply by 0xFF, which runs on
+// the FMA pipe and spares the integer ALU pipe).  c[k] holds key k's 16
+// coordinate bytes (coordinate i = byte i % 4 of word i / 4).
+__device__ __forceinline__ void hilbert_keys4(const uint4 (&c)[4], uint64_t (&hi)[4],
+                                              uint64_t (&lo)[4]) {
+    constexpr uint32_t ONES = 0x01010101u;
+    uint32_t X[16];
+    {
+        const uint32_t w[4][4] = {{c[0].x, c[0].y, c[0].z, c[0].w},
+                                  {c[1].x, c[1].y, c[1].z, c[1].w},
+                                  {c[2].x, c[2].y, c[2].z, c[2].w},
+                                  {c[3].x, c[3].y, c[3].z, c[3].w}};
+#pragma unroll
+        for (int wi = 0; wi < 4; ++wi) {
+            uint32_t t[4];
+            transpose4x4_bytes(w[0][wi], w[1][wi], w[2][wi], w[3][wi], t);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) X[4 * wi + b] = t[b];
+        }
+    }
+#pragma unroll
+    for (int q = 7; q >= 1; --q) {
+        const uint32_t low = ((1u << q) - 1u) * ONES;
+        X[0] ^= low & (((X[0] >> q) & ONES) * 0xFFu);
+#pragma unroll
+        for (int i = 1; i < 16; ++i) {
+            const uint32_t set = ((X[i] >> q) & ONES) * 0xFFu;
+            const uint32_t d = (X[0] ^ X[i]) & low;
+            X[0] ^= (set & low) | (~set & d);
+            X[i] ^= d & ~set;
+        }
+    }
+#pragma unroll
+    for (int i = 1; i < 16; ++i) X[i] ^= X[i - 1];
+    uint32_t corr = (X[15] >> 1) & 0x7F7F7F7Fu;
+    corr ^= (corr >> 1) & 0x7F7F7F7Fu;
+    corr ^= (corr >> 2) & 0x3F3F3F3Fu;
+    corr ^= (corr >> 4) & 0x0F0F0F0Fu;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) X[i] ^= corr;
+    // back to one 16-byte group per key, then the bit-plane transposes
+    uint32_t y[4][4];   // y[g][k]: axes 4g..4g+3 of key k
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+        transpose4x4_bytes(X[4 * g], X[4 * g + 1], X[4 * g + 2], X[4 * g + 3], y[g]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t A = transpose8x8((uint64_t)y[0][k] | ((uint64_t)y[1][k] << 32));
+        const uint64_t B = transpose8x8((uint64_t)y[2][k] | ((uint64_t)y[3][k] << 32));
+        const uint32_t Al = (uint32_t)A, Ah = (uint32_t)(A >> 32);
+        const uint32_t Bl = (uint32_t)B, Bh = (uint32_t)(B >> 32);
+        hi[k] = ((uint64_t)__brev(__byte_perm(Ah, Bh, 0x6273)) << 32) |
+                __brev(__byte_perm(Ah, Bh, 0x4051));
+        lo[k] = ((uint64_t)__brev(__byte_perm(Al, Bl, 0x6273)) << 32) |
+                __brev(__byte_perm(Al, Bl, 0x4051));
+    }
+}
+
 __device__ __forceinline__ void hilbert_key_m(uint32_t m, uint32_t (&X)[16], uint64_t& hi,
                                               uint64_t& lo) {
     switch (m) {
@@ -126,6 +197,21 @@ __device__ __forceinline__ uint32_t quantize_coord(float x) {
     if (!(s > 0.0f)) return 0u;
     if (s >= 255.0f) return 255u;
     return __float2uint_rn(s);
+}
+
+// The 16 coordinate bytes of curve c (consecutive dims, m = 16) of a row.
+__device__ __forceinline__ uint4 curve_bytes16(const void* row, hc_dtype dtype, uint32_t c) {
+    if (dtype == HC_U8)
+        return __ldg(reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(row) + (size_t)c * 16));
+    const float4* f = reinterpret_cast<const float4*>(static_cast<const float*>(row) + (size_t)c * 16);
+    uint32_t w[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float4 v = __ldg(f + t);
+        w[t] = quantize_coord(v.x) | (quantize_coord(v.y) << 8) | (quantize_coord(v.z) << 16) |
+               (quantize_coord(v.w) << 24);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // proj[j] <- v[a[c][j]] for the m coordinates of curve c, as 8-bit values.

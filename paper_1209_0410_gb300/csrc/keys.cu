@@ -13,7 +13,25 @@ __global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
         const uint32_t part = partition_of(r, a.n, a.partitions);
         const uint64_t local = r - partition_start(part, a.n, a.partitions);
         const void* row = static_cast<const uint8_t*>(a.db) + r * a.row_bytes;
-        for (uint32_t c = 0; c < a.P.curves; ++c) {
+        uint32_t c = 0;
+        if (a.P.m == 16 && a.P.dim_map == nullptr) {
+            // four curves at a time, SIMD within a register
+            for (; c + 4 <= a.P.curves; c += 4) {
+                uint4 cb[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cb[t] = curve_bytes16(row, a.P.dtype, c + t);
+                uint64_t hi[4], lo[4];
+                hilbert_keys4(cb, hi, lo);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint64_t g = a.list_off[part * a.P.curves + c + t] + local;
+                    a.hi[g] = hi[t];
+                    a.lo[g] = lo[t];
+                    if (a.ids) a.ids[g] = (uint32_t)r;
+                }
+            }
+        }
+        for (; c < a.P.curves; ++c) {
             uint64_t hi, lo;
             curve_key(row, a.P, c, hi, lo);
             const uint64_t g = a.list_off[part * a.P.curves + c] + local;

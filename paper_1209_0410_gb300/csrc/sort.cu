@@ -144,19 +144,65 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const SegInfo* __restric
     }
 }
 
-// Shared memory of one scatter tile: words and positions in sorted order, the
-// positions in input order, and per-warp digit counters (16-bit: a warp
-// ranks 512 records, a tile 4096).
+// One scatter tile in shared memory: the words and positions of the tile
+// (padded so that blocked and striped accesses are free of bank conflicts),
+// the per-thread nibble counters, and per-digit bases.
+constexpr int kPadW = kTile + kTile / 16;   // one spare word slot per 16
+constexpr int kPadP = kTile + kTile / 32;   // one spare position slot per 32
+__device__ __forceinline__ int padw(int i) { return i + (i >> 4); }
+__device__ __forceinline__ int padp(int i) { return i + (i >> 5); }
+
 struct ScatterSmem {
-    uint64_t sw[kTile];
-    uint32_t sp[kTile];
-    uint32_t sp_in[kTile];
-    uint16_t whist[kSWarps][256];
+    uint64_t w[kPadW];
+    uint32_t p[kPadP];
+    uint16_t cnt[16][kSThreads];   // nibble counts, then exclusive bases
+    uint64_t gbase[256];
+    uint16_t dstart[256];
+    uint32_t warp_sums[kSWarps];
 };
 
-// Two 512-thread blocks per SM: the words stay in registers (two per
-// record), the in-warp offsets are packed two per register, the positions
-// wait in shared memory.
+// Stable counting sort of the tile by a 4-bit slice of the digit: each thread
+// owns records 8t..8t+7 (in registers), counts its nibbles in 4-bit fields of
+// one 64-bit register, the 16 x 512 counts are scanned bucket-major, and each
+// record lands at its bucket base + its rank among the thread's earlier
+// records of that bucket.
+__device__ __forceinline__ void nibble_pass(ScatterSmem& sm, const uint64_t (&w)[kIpt],
+                                            const uint32_t (&p)[kIpt], int nshift) {
+    const int t = threadIdx.x;
+    uint64_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) cnt += 1ull << (4 * ((w[j] >> nshift) & 0xF));
+#pragma unroll
+    for (int b = 0; b < 16; ++b) sm.cnt[b][t] = (uint16_t)((cnt >> (4 * b)) & 0xF);
+    __syncthreads();
+    // bucket-major exclusive scan: thread t owns entries [16t, 16t + 16)
+    uint16_t* flat = &sm.cnt[0][0];
+    uint32_t vals[16];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        vals[e] = flat[16 * t + e];
+        sum += vals[e];
+    }
+    uint32_t run = block_exclusive_scan<kSWarps>(sum, sm.warp_sums);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        flat[16 * t + e] = (uint16_t)run;
+        run += vals[e];
+    }
+    __syncthreads();
+    uint64_t seen = 0;
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t b = (uint32_t)(w[j] >> nshift) & 0xF;
+        const uint32_t rank = sm.cnt[b][t] + (uint32_t)((seen >> (4 * b)) & 0xF);
+        seen += 1ull << (4 * b);
+        sm.w[padw(rank)] = w[j];
+        sm.p[padp(rank)] = p[j];
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
     const uint64_t* __restrict__ wsrc, const uint32_t* __restrict__ psrc,
     uint64_t* __restrict__ wdst, uint32_t* __restrict__ pdst, int shift, uint32_t nseg,
@@ -164,95 +210,58 @@ __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
     const uint32_t* __restrict__ totals) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
-    __shared__ uint16_t dstart[256];
-    __shared__ uint64_t gbase[256];
-    __shared__ uint32_t warp_sums[kSWarps];
 
     SegInfo si;
     uint32_t seg, lt, count;
     uint64_t start;
     tile_of(nseg, segs, si, seg, lt, start, count);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lanemask_lt = (1u << lane) - 1u;
+    const int t = threadIdx.x;
 
-    for (int t = threadIdx.x; t < kSWarps * 256; t += kSThreads)
-        (&sm.whist[0][0])[t] = 0;
-
-    uint64_t wv[kIpt];
+    // blocked records; past the tile's end: digit 255 and last in order
+    uint64_t w[kIpt];
+    uint32_t p[kIpt];
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
-        const uint32_t i = warp * kWarpItems + j * 32 + lane;
+        const uint32_t i = (uint32_t)t * kIpt + j;
         const bool valid = i < count;
-        wv[j] = valid ? __ldg(wsrc + start + i) : 0ull;
-        if (valid) sm.sp_in[i] = psrc ? __ldg(psrc + start + i) : (uint32_t)(start + i);
+        w[j] = valid ? __ldg(wsrc + start + i) : (0xFFull << shift);
+        p[j] = valid ? (psrc ? __ldg(psrc + start + i) : (uint32_t)(start + i)) : 0u;
     }
-    __syncthreads();
-
-    // stable ranking inside the warp's 512 consecutive records, round by round
-    uint32_t offp[kIpt / 2];
+    // the digit is bits [shift, shift + 8) of the word: low nibble, then high
+    nibble_pass(sm, w, p, shift);
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
-        const uint32_t i = warp * kWarpItems + j * 32 + lane;
-        const bool valid = i < count;
-        const uint32_t dg = valid ? (uint32_t)(wv[j] >> shift) & 0xFFu : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t rank = __popc(peers & lanemask_lt);
-        const uint32_t base = valid ? sm.whist[warp][dg] : 0u;
-        __syncwarp();
-        if (valid && rank == 0) sm.whist[warp][dg] = (uint16_t)(base + __popc(peers));
-        __syncwarp();
-        const uint32_t off = base + rank;
-        if (j & 1)
-            offp[j >> 1] |= off << 16;
-        else
-            offp[j >> 1] = off;
+        const int i = t * kIpt + j;
+        w[j] = sm.w[padw(i)];
+        p[j] = sm.p[padp(i)];
     }
     __syncthreads();
+    nibble_pass(sm, w, p, shift + 4);
 
-    // per digit: offsets of each warp's run, the tile's digit starts, and the
-    // global base of the digit's run for this tile
+    // where each digit's run starts in the sorted tile
+    for (uint32_t i = t; i < count; i += kSThreads) {
+        const uint32_t d = (uint32_t)(sm.w[padw(i)] >> shift) & 0xFFu;
+        if (i == 0 || ((uint32_t)(sm.w[padw(i - 1)] >> shift) & 0xFFu) != d)
+            sm.dstart[d] = (uint16_t)i;
+    }
     {
-        // threads 0..255 own one digit each; the rest add zeros to the scans
-        const uint32_t dg = threadIdx.x;
+        // threads 0..255 own one digit each; the rest add zeros to the scan
+        const uint32_t dg = t;
         const bool own = dg < 256;
-        uint32_t run = 0;
-        if (own) {
-#pragma unroll
-            for (int w = 0; w < kSWarps; ++w) {
-                const uint32_t c = sm.whist[w][dg];
-                sm.whist[w][dg] = (uint16_t)run;
-                run += c;
-            }
-        }
-        const uint32_t tile_start = block_exclusive_scan<kSWarps>(run, warp_sums);
         const uint32_t seg_prefix = block_exclusive_scan<kSWarps>(
-            own ? __ldg(totals + (uint64_t)seg * 256 + dg) : 0u, warp_sums);
+            own ? __ldg(totals + (uint64_t)seg * 256 + dg) : 0u, sm.warp_sums);
         if (own) {
-            dstart[dg] = (uint16_t)tile_start;
             const uint32_t before = __ldg(counts + si.cnt_base + (uint64_t)dg * si.ntiles + lt);
-            gbase[dg] = si.start + seg_prefix + before - tile_start;
+            sm.gbase[dg] = si.start + seg_prefix + before;
         }
     }
     __syncthreads();
-
-#pragma unroll
-    for (int j = 0; j < kIpt; ++j) {
-        const uint32_t i = warp * kWarpItems + j * 32 + lane;
-        if (i < count) {
-            const uint32_t dg = (uint32_t)(wv[j] >> shift) & 0xFFu;
-            const uint32_t off = (offp[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
-            const uint32_t pos = (uint32_t)dstart[dg] + sm.whist[warp][dg] + off;
-            sm.sw[pos] = wv[j];
-            sm.sp[pos] = sm.sp_in[i];
-        }
-    }
-    __syncthreads();
-
-    for (uint32_t i = threadIdx.x; i < count; i += kSThreads) {
-        const uint64_t v = sm.sw[i];
-        const uint64_t g = gbase[(uint32_t)(v >> shift) & 0xFFu] + i;
+    for (uint32_t i = t; i < count; i += kSThreads) {
+        const uint64_t v = sm.w[padw(i)];
+        const uint32_t d = (uint32_t)(v >> shift) & 0xFFu;
+        const uint64_t g = sm.gbase[d] + (i - sm.dstart[d]);
         wdst[g] = v;
-        pdst[g] = sm.sp[i];
+        pdst[g] = sm.p[padp(i)];
     }
 }
 
