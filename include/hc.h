@@ -149,6 +149,16 @@ HC_API int hc_query_depths(hc_index* idx, const void* q_dev, uint32_t nq, uint32
                            const uint32_t* p_dev, int32_t* out_ids_dev, void* out_dist_dev,
                            void* cuda_stream);
 
+/*
+ * hc_query_at -- hc_query with the lower_bound step done beforehand:
+ * pos_dev holds the nq x lists int64 positions of hc_query_positions for the
+ * same queries (any other values give windows around those positions).  The
+ * kernel then only gathers, ranks and selects.  No allocation; asynchronous.
+ */
+HC_API int hc_query_at(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
+                       const int64_t* pos_dev, int32_t* out_ids_dev, void* out_dist_dev,
+                       void* cuda_stream);
+
 /* hc_free -- releases an index and everything it owns (not db_dev).  The
  * caller makes sure no work using the index is still queued.  NULL is ok. */
 HC_API void hc_free(hc_index* idx);

@@ -303,6 +303,20 @@ HC_API int hc_query_depths(hc_index* idx, const void* q_dev, uint32_t nq, uint32
                                   static_cast<cudaStream_t>(cuda_stream), p_dev));
 }
 
+HC_API int hc_query_at(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
+                       const int64_t* pos_dev, int32_t* out_ids_dev, void* out_dist_dev,
+                       void* cuda_stream) {
+    if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
+    if (nq == 0) return HC_OK;
+    if (!q_dev || !pos_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev))
+        return HC_ERR_ARG;
+    if (!is_device_ptr(q_dev) || !is_device_ptr(pos_dev) || !is_device_ptr(out_ids_dev) ||
+        !is_device_ptr(out_dist_dev))
+        return HC_ERR_ARG;
+    return status_of(launch_query(view_of(idx), q_dev, nq, k, p, out_ids_dev, out_dist_dev,
+                                  static_cast<cudaStream_t>(cuda_stream), nullptr, pos_dev));
+}
+
 HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids_host, void* out_dist_host, void* cuda_stream) {
     if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;

@@ -83,9 +83,11 @@ struct IndexView {
 };
 
 // p_query (device, nq entries, nullable) gives each query its own depth.
+// pos_in (device, nq x lists, nullable): lower_bound positions computed
+// earlier (hc_query_positions), so the kernel skips its own search.
 cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids, void* out_dist, cudaStream_t s,
-                         const uint32_t* p_query = nullptr);
+                         const uint32_t* p_query = nullptr, const int64_t* pos_in = nullptr);
 cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, int64_t* pos,
                              cudaStream_t s);
 cudaError_t launch_bruteforce(const void* db, hc_dtype dtype, uint64_t n, uint32_t d,

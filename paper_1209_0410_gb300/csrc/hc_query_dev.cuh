@@ -63,9 +63,13 @@ __device__ __forceinline__ Acc reduce_scatter(Acc (&v)[LPR], uint32_t s) {
 
 // Candidates produced per lane by one 32-row chunk: rows wider than 8 lanes
 // are reduced 8 sub-batches at a time, leaving one candidate per group.
+#ifndef HC_GROUP_MAX
+#define HC_GROUP_MAX 8   // sub-batches (rows per lane group) loaded before reducing
+#endif
+
 template <int LPR>
 struct ChunkWidth {
-    static constexpr int G = LPR < 8 ? LPR : 8;   // sub-batches reduced together
+    static constexpr int G = LPR < HC_GROUP_MAX ? LPR : HC_GROUP_MAX;
     static constexpr int NG = LPR / G;            // groups, candidates per lane
 };
 
@@ -140,7 +144,7 @@ __device__ __forceinline__ uint64_t chunk_candidates(const uint8_t* __restrict__
                                                      uint32_t row_bytes, const uint8_t* qrow,
                                                      uint4 qv0, uint32_t id, uint32_t cnt,
                                                      int lane) {
-    static_assert(LPR <= 8, "wider rows give several candidates per lane");
+    static_assert(ChunkWidth<LPR>::NG == 1, "wider rows give several candidates per lane");
     uint64_t out[1];
     chunk_candidates_n<F32, LPR>(db, row_bytes, qrow, qv0, id, cnt, lane, out);
     return out[0];
@@ -197,8 +201,14 @@ template <bool F32, int LPR, int KR>
 __device__ __forceinline__ void search_lists(const IndexView& ix, const uint8_t* qrow,
                                              uint32_t depth, uint32_t k, uint32_t L0,
                                              uint32_t Lstep, uint32_t* pos_w, WarpTopK<KR>& top,
-                                             int lane) {
-    query_positions(ix, qrow, pos_w, lane, L0, Lstep);
+                                             int lane, const int64_t* pos_in = nullptr) {
+    if (pos_in) {
+        for (uint32_t L = L0 + (uint32_t)lane * Lstep; L < ix.lists; L += 32 * Lstep)
+            pos_w[L] = (uint32_t)__ldg(pos_in + L);
+        __syncwarp();
+    } else {
+        query_positions(ix, qrow, pos_w, lane, L0, Lstep);
+    }
     const uint32_t s = (uint32_t)lane % LPR;
     const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
     const uint8_t* db = static_cast<const uint8_t*>(ix.db);

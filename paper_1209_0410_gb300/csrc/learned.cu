@@ -363,10 +363,16 @@ __device__ void query_features(const IndexView& ix, const uint8_t* qrow, uint4 q
         const uint32_t lo = pos > 4 ? pos - 4 : 0u, hi = pos + 4 < n ? pos + 4 : n;
         const uint32_t cnt = hi - lo;
         const uint32_t id = (uint32_t)lane < cnt ? __ldg(ix.ids + off + lo + lane) : 0u;
-        const uint64_t cand = chunk_candidates<false, 8>(db, ix.row_bytes, qrow, qv0, id, cnt, lane);
-        const bool valid = cand != kEmpty;
-        uint32_t dmin = valid ? (uint32_t)(cand >> 32) : 0xFFFFFFFFu;
-        uint64_t dsum = valid ? (cand >> 32) : 0ull;
+        uint64_t cands[ChunkWidth<8>::NG];
+        chunk_candidates_n<false, 8>(db, ix.row_bytes, qrow, qv0, id, cnt, lane, cands);
+        uint32_t dmin = 0xFFFFFFFFu;
+        uint64_t dsum = 0;
+#pragma unroll
+        for (int g = 0; g < ChunkWidth<8>::NG; ++g)
+            if (cands[g] != kEmpty) {
+                dmin = min(dmin, (uint32_t)(cands[g] >> 32));
+                dsum += cands[g] >> 32;
+            }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));

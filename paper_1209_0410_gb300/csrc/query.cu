@@ -37,10 +37,16 @@ struct QueryArgs {
     void* out_dist;
     int64_t* out_pos;            // positions-only kernel
     const uint32_t* p_query;     // per-query depth (overrides p), or null
+    const int64_t* pos_in;       // precomputed lower_bound positions (nq x lists), or null
 };
 
+#ifndef HC_QUERY_MIN_BLOCKS
+#define HC_QUERY_MIN_BLOCKS 3    // resident blocks per SM the query kernel is compiled for
+                                 // (3 x 8 warps: best at p = 128 and 512 on GB300)
+#endif
+
 template <bool F32, int LPR, int KR>
-__global__ void __launch_bounds__(kQWarps * 32) query_kernel(QueryArgs a) {
+__global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kernel(QueryArgs a) {
     extern __shared__ uint32_t s_pos[];  // kQWarps x lists
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t qi = blockIdx.x * kQWarps + warp;
@@ -50,7 +56,8 @@ __global__ void __launch_bounds__(kQWarps * 32) query_kernel(QueryArgs a) {
     const uint32_t depth = a.p_query ? __ldg(a.p_query + qi) : a.p;
     WarpTopK<KR> top;
     top.init();
-    search_lists<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, top, lane);
+    search_lists<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, top, lane,
+                               a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
     top.template store<F32>(a.k, lane, a.out_ids + (size_t)qi * a.k,
                             static_cast<uint32_t*>(a.out_dist) + (size_t)qi * a.k);
 }
@@ -147,9 +154,9 @@ struct BruteLaunch {
 
 cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids, void* out_dist, cudaStream_t s,
-                         const uint32_t* p_query) {
+                         const uint32_t* p_query, const int64_t* pos_in) {
     if (nq == 0) return cudaSuccess;
-    QueryArgs a{ix, q, nq, k, p, out_ids, out_dist, nullptr, p_query};
+    QueryArgs a{ix, q, nq, k, p, out_ids, out_dist, nullptr, p_query, pos_in};
     return dispatch<QueryLaunch>(ix.P.dtype == HC_F32, lanes_per_row(ix.row_bytes), regs_for_k(k),
                                  a, s);
 }
@@ -157,7 +164,7 @@ cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32
 cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, int64_t* pos,
                              cudaStream_t s) {
     if (nq == 0) return cudaSuccess;
-    QueryArgs a{ix, q, nq, 1, 0, nullptr, nullptr, pos, nullptr};
+    QueryArgs a{ix, q, nq, 1, 0, nullptr, nullptr, pos, nullptr, nullptr};
     const unsigned blocks = (nq + kQWarps - 1) / kQWarps;
     positions_kernel<<<blocks, kQWarps * 32, sizeof(uint32_t) * kQWarps * ix.lists, s>>>(a);
     count_launches(1);

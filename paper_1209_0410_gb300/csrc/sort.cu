@@ -163,40 +163,54 @@ struct ScatterSmem {
 
 // Stable counting sort of the tile by a 4-bit slice of the digit: each thread
 // owns records 8t..8t+7 (in registers), counts its nibbles in 4-bit fields of
-// one 64-bit register, the 16 x 512 counts are scanned bucket-major, and each
-// record lands at its bucket base + its rank among the thread's earlier
-// records of that bucket.
+// two 32-bit registers (buckets 0-7, 8-15), the 16 x 512 counts are scanned
+// bucket-major (each thread scans a 32-byte slice with two 16-byte accesses),
+// and each record lands at its bucket base + its rank among the thread's
+// earlier records of that bucket.
 __device__ __forceinline__ void nibble_pass(ScatterSmem& sm, const uint64_t (&w)[kIpt],
-                                            const uint32_t (&p)[kIpt], int nshift) {
+                                            const uint32_t (&p)[kIpt],
+                                            const uint32_t (&dg)[kIpt], int nshift) {
     const int t = threadIdx.x;
-    uint64_t cnt = 0;
-#pragma unroll
-    for (int j = 0; j < kIpt; ++j) cnt += 1ull << (4 * ((w[j] >> nshift) & 0xF));
-#pragma unroll
-    for (int b = 0; b < 16; ++b) sm.cnt[b][t] = (uint16_t)((cnt >> (4 * b)) & 0xF);
-    __syncthreads();
-    // bucket-major exclusive scan: thread t owns entries [16t, 16t + 16)
-    uint16_t* flat = &sm.cnt[0][0];
-    uint32_t vals[16];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        vals[e] = flat[16 * t + e];
-        sum += vals[e];
-    }
-    uint32_t run = block_exclusive_scan<kSWarps>(sum, sm.warp_sums);
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        flat[16 * t + e] = (uint16_t)run;
-        run += vals[e];
-    }
-    __syncthreads();
-    uint64_t seen = 0;
+    uint32_t c0 = 0, c1 = 0;
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
-        const uint32_t b = (uint32_t)(w[j] >> nshift) & 0xF;
-        const uint32_t rank = sm.cnt[b][t] + (uint32_t)((seen >> (4 * b)) & 0xF);
-        seen += 1ull << (4 * b);
+        const uint32_t b = (dg[j] >> nshift) & 0xF;
+        const uint32_t inc = 1u << (4 * (b & 7));
+        c0 += b < 8 ? inc : 0u;
+        c1 += b < 8 ? 0u : inc;
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        sm.cnt[b][t] = (uint16_t)((c0 >> (4 * b)) & 0xF);
+        sm.cnt[b + 8][t] = (uint16_t)((c1 >> (4 * b)) & 0xF);
+    }
+    __syncthreads();
+    // bucket-major exclusive scan: thread t owns entries [16t, 16t + 16)
+    uint4* slice = reinterpret_cast<uint4*>(&sm.cnt[0][0]) + 2 * t;
+    const uint4 s0 = slice[0], s1 = slice[1];
+    const uint32_t words[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    uint32_t sum = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sum += (words[e] & 0xFFFFu) + (words[e] >> 16);
+    uint32_t run = block_exclusive_scan<kSWarps>(sum, sm.warp_sums);
+    uint32_t out[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const uint32_t a = words[e] & 0xFFFFu, b = words[e] >> 16;
+        out[e] = run | ((run + a) << 16);
+        run += a + b;
+    }
+    slice[0] = make_uint4(out[0], out[1], out[2], out[3]);
+    slice[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    __syncthreads();
+    uint32_t s0c = 0, s1c = 0;   // records of the thread seen so far, per bucket
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+        const uint32_t b = (dg[j] >> nshift) & 0xF;
+        const uint32_t sh = 4 * (b & 7);
+        const uint32_t seen = ((b < 8 ? s0c : s1c) >> sh) & 0xF;
+        const uint32_t rank = sm.cnt[b][t] + seen;
+        if (b < 8) s0c += 1u << sh; else s1c += 1u << sh;
         sm.w[padw(rank)] = w[j];
         sm.p[padp(rank)] = p[j];
     }
@@ -228,15 +242,19 @@ __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
         p[j] = valid ? (psrc ? __ldg(psrc + start + i) : (uint32_t)(start + i)) : 0u;
     }
     // the digit is bits [shift, shift + 8) of the word: low nibble, then high
-    nibble_pass(sm, w, p, shift);
+    uint32_t dg[kIpt];
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) dg[j] = (uint32_t)(w[j] >> shift) & 0xFFu;
+    nibble_pass(sm, w, p, dg, 0);
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
         const int i = t * kIpt + j;
         w[j] = sm.w[padw(i)];
         p[j] = sm.p[padp(i)];
+        dg[j] = (uint32_t)(w[j] >> shift) & 0xFFu;
     }
     __syncthreads();
-    nibble_pass(sm, w, p, shift + 4);
+    nibble_pass(sm, w, p, dg, 4);
 
     // where each digit's run starts in the sorted tile
     for (uint32_t i = t; i < count; i += kSThreads) {

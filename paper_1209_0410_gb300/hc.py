@@ -93,6 +93,7 @@ def lib():
         L.hc_query_positions.argtypes = [_vp, _vp, _u32, _vp, _vp]
         L.hc_bruteforce.argtypes = [_vp, ctypes.c_int, _u64, _u32, _vp, _u32, _u32, _vp, _vp, _vp]
         L.hc_query_depths.argtypes = [_vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]
+        L.hc_query_at.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp, _vp]
         L.hc_serve_create_ex.argtypes = [ctypes.POINTER(_vp), _u32, _u64,
                                          ctypes.POINTER(_ServeParams), ctypes.POINTER(_vp)]
         L.hc_serve_create.argtypes = [ctypes.POINTER(_vp), _u32, _u64, ctypes.POINTER(_vp)]
@@ -247,6 +248,20 @@ def hc_query(index, q, k, p, out_ids=None, out_dist=None, stream=None):
     if nq:
         _check(lib().hc_query(index.handle, _dev(q, "q"), nq, k, p, _dev(out_ids, "out_ids"),
                               _dev(out_dist, "out_dist"), _stream(stream)), "hc_query")
+    return out_ids, out_dist
+
+
+def hc_query_at(index, q, k, p, positions, out_ids=None, out_dist=None, stream=None):
+    """hc_query with positions from hc_query_positions ((nq, lists) int64)."""
+    nq = q.shape[0]
+    if out_ids is None:
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=_dist_dtype(index.dtype), device=q.device)
+    if nq:
+        _check(lib().hc_query_at(index.handle, _dev(q, "q"), nq, k, p, _dev(positions, "pos"),
+                                 _dev(out_ids, "out_ids"), _dev(out_dist, "out_dist"),
+                                 _stream(stream)), "hc_query_at")
     return out_ids, out_dist
 
 

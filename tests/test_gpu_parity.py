@@ -372,3 +372,17 @@ def test_injected_allocation_failure_reports_oom(hc):
     oidx = O.build(db, curves=8, m=16)
     rids, _ = O.search(oidx, db, q, 5, 16)
     assert np.array_equal(ids.cpu().numpy(), rids)
+
+
+def test_query_at_precomputed_positions(hc):
+    """hc_query_positions + hc_query_at = hc_query, bit for bit."""
+    import torch
+    n, nq = 20011, 333
+    db, q = make_case(n, nq, seed=17)
+    idx = hc.hc_build(dev(db))
+    tq = dev(q)
+    pos = hc.hc_query_positions(idx, tq)
+    ids, dist = hc.hc_query_at(idx, tq, 10, 64, pos)
+    rids, rdist = hc.hc_query(idx, tq, 10, 64)
+    torch.cuda.synchronize()
+    assert torch.equal(ids, rids) and torch.equal(dist, rdist)
