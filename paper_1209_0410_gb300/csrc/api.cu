@@ -167,6 +167,7 @@ int build_index(hc_index* x, cudaStream_t s) {
     sp.seg_off_dev = x->list_off_dev;
     sp.key_bits = 8 * P.dims_per_curve;
     sp.allow_sync = true;
+    sp.hi_skip = 1;   // runs of equal top-56-bit prefixes are a few records long
     sp.out_hi = x->keys_hi;
     sp.out_lo = x->keys_lo;
     sp.out_ids = x->ids;
@@ -447,6 +448,7 @@ HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
     sp.seg_off.assign(seg_off_host, seg_off_host + nseg + 1);
     sp.key_bits = key_bits;
     sp.allow_sync = true;   // this entry point synchronises anyway
+    sp.hi_skip = 1;
     const size_t out_bytes = (sizeof(uint64_t) * 2 + sizeof(uint32_t)) * total;
     const size_t off_bytes = sizeof(uint64_t) * (nseg + 1);
     const size_t head = ((out_bytes + 255) & ~(size_t)255) + ((off_bytes + 255) & ~(size_t)255);

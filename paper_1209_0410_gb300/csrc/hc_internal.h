@@ -52,6 +52,9 @@ struct SortProblem {
     // equal high words is too long for the high-word-first path)?  With
     // false, every digit is sorted and nothing waits on the device.
     bool allow_sync = false;
+    // On that path, low digits of the high word left to the run fix-up (runs
+    // of records whose other high-word bits are equal); 0 sorts every digit.
+    int hi_skip = 0;
     const uint64_t* id_base_dev = nullptr;  // device, nseg: ids[i] = id_base[s] + i - seg start
                                             // (then `ids` is not read); null = gather ids
     uint64_t* out_hi;          // device, total records (distinct from sources)

@@ -329,19 +329,20 @@ __global__ void __launch_bounds__(256) gather_final_kernel(
     }
 }
 
-// Runs of records whose high words are equal must end ordered by (low word,
-// position); after sorting by the high word alone they are in position order.
-// One tile per block: a record outside any run is written in place; a record
-// in a run of at most kMaxRun finds the run's bounds, ranks itself among the
-// run's (low word, position) pairs and is written at run start + rank.  A
-// longer run sets *long_run, and the caller redoes the sort with every digit.
+// After sorting by the high word's top bytes alone (records with equal
+// prefixes w >> run_shift stay in position order), runs of equal prefixes
+// must end ordered by (high word, low word, position).  One tile per block: a
+// record outside any run is written in place; a record in a run of at most
+// kMaxRun finds the run's bounds, ranks itself among the run's records and is
+// written at run start + rank.  A longer run sets *long_run, and the caller
+// redoes the sort with every digit.  The low words and ids are gathered here.
 constexpr uint32_t kMaxRun = 32;
 
 __global__ void __launch_bounds__(256) fixup_final_kernel(
-    const uint64_t* __restrict__ w, const uint32_t* __restrict__ pos,
-    const uint64_t* __restrict__ lo, FinalIds fid, uint64_t* __restrict__ out_lo,
-    uint32_t* __restrict__ out_ids, uint32_t nseg, const SegInfo* __restrict__ segs,
-    uint32_t* __restrict__ long_run) {
+    const uint64_t* __restrict__ w, int run_shift, const uint32_t* __restrict__ pos,
+    const uint64_t* __restrict__ lo, FinalIds fid, uint64_t* __restrict__ out_hi,
+    uint64_t* __restrict__ out_lo, uint32_t* __restrict__ out_ids, uint32_t nseg,
+    const SegInfo* __restrict__ segs, uint32_t* __restrict__ long_run) {
     SegInfo si;
     uint32_t seg, lt, count;
     uint64_t start;
@@ -351,29 +352,37 @@ __global__ void __launch_bounds__(256) fixup_final_kernel(
     for (uint32_t t = threadIdx.x; t < count; t += blockDim.x) {
         const uint64_t i = start + t;
         const uint64_t wi = __ldg(w + i);
+        const uint64_t key = wi >> run_shift;
         const uint32_t pi = __ldg(pos + i);
         const uint64_t li = __ldg(lo + pi);
         const uint32_t idi = fid.id_base ? (uint32_t)(id_base + pi) : __ldg(fid.ids + pi);
-        const bool prev_eq = i > si.start && __ldg(w + i - 1) == wi;
-        const bool next_eq = i + 1 < seg_end && __ldg(w + i + 1) == wi;
+        const bool prev_eq = i > si.start && (__ldg(w + i - 1) >> run_shift) == key;
+        const bool next_eq = i + 1 < seg_end && (__ldg(w + i + 1) >> run_shift) == key;
         uint64_t dst = i;
         if (prev_eq || next_eq) {
             uint64_t rs = i, re = i + 1;
-            while (rs > si.start && i - rs <= kMaxRun && __ldg(w + rs - 1) == wi) --rs;
-            while (re < seg_end && re - i <= kMaxRun && __ldg(w + re) == wi) ++re;
+            while (rs > si.start && i - rs <= kMaxRun && (__ldg(w + rs - 1) >> run_shift) == key)
+                --rs;
+            while (re < seg_end && re - i <= kMaxRun && (__ldg(w + re) >> run_shift) == key) ++re;
             if (re - rs > kMaxRun) {
                 atomicOr(long_run, 1u);
             } else {
                 uint32_t rank = 0;
                 for (uint64_t j = rs; j < re; ++j) {
                     if (j == i) continue;
+                    const uint64_t wj = __ldg(w + j);
                     const uint32_t pj = __ldg(pos + j);
-                    const uint64_t lj = __ldg(lo + pj);
-                    rank += (lj < li || (lj == li && pj < pi)) ? 1u : 0u;
+                    bool before = wj < wi;
+                    if (wj == wi) {
+                        const uint64_t lj = __ldg(lo + pj);
+                        before = lj < li || (lj == li && pj < pi);
+                    }
+                    rank += before ? 1u : 0u;
                 }
                 dst = rs + rank;
             }
         }
+        out_hi[dst] = wi;
         out_lo[dst] = li;
         out_ids[dst] = idi;
     }
@@ -485,13 +494,16 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     uint32_t* flag = reinterpret_cast<uint32_t*>(base + L.off_flag);
 
     if (p.allow_sync && hi_passes > 0 && L.ntiles) {
-        // sort by the high word alone, then order runs of equal high words
-        uint64_t* wb[2] = {p.out_hi, wtmp};
-        int wn = (hi_passes % 2 == 1) ? 0 : 1;   // the last pass writes out_hi
+        // sort by the high word's top bytes alone (skipping its lowest
+        // hi_skip digits when more remain), then order runs of equal prefixes
+        const int skip = (p.hi_skip > 0 && hi_passes > p.hi_skip) ? p.hi_skip : 0;
+        const int npass = hi_passes - skip;
+        uint64_t* wb[2] = {wtmp, p.out_hi};
+        int wn = (npass % 2 == 1) ? 0 : 1;   // the last pass writes wtmp
         int pn = 0;
         const uint64_t* cw = p.hi;
         const uint32_t* cp = nullptr;
-        for (int t = 8; t < 8 + hi_passes; ++t) {
+        for (int t = 8 + skip; t < 8 + hi_passes; ++t) {
             const int shift = (t & 7) * 8;
             hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cw, shift, L.nseg, segs, counts);
             scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
@@ -505,11 +517,11 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             wn ^= 1;
             pn ^= 1;
         }
-        if (cw != p.out_hi) return HC_ERR_STATE;
+        if (cw != wtmp) return HC_ERR_STATE;
         if (cudaMemsetAsync(flag, 0, sizeof(uint32_t), s) != cudaSuccess) return HC_ERR_CUDA;
-        fixup_final_kernel<<<L.ntiles, 256, 0, s>>>(p.out_hi, cp, p.lo,
-                                                     FinalIds{p.ids, p.id_base_dev}, p.out_lo,
-                                                     p.out_ids, L.nseg, segs, flag);
+        fixup_final_kernel<<<L.ntiles, 256, 0, s>>>(wtmp, 8 * skip, cp, p.lo,
+                                                     FinalIds{p.ids, p.id_base_dev}, p.out_hi,
+                                                     p.out_lo, p.out_ids, L.nseg, segs, flag);
         count_launches(1);
         if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
         uint32_t long_run = 1;

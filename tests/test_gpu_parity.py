@@ -70,7 +70,7 @@ def test_hilbert_keys_bit_exact(hc, m, curves, mapped, dtype):
 
 # ------------------------------------------------------------------ K2
 SORT_CASES = ["random", "duplicates", "narrow", "ragged", "reversed_ids", "runs32", "runs33",
-              "hi_ties"]
+              "hi_ties", "prefix_ties"]
 
 
 @pytest.mark.parametrize("case", SORT_CASES)
@@ -82,7 +82,7 @@ def test_sort_keys_matches_stable_sort(hc, case):
     sizes = {"random": [30000], "duplicates": [20000, 5000], "narrow": [12289],
              "ragged": [0, 1, 4095, 4096, 4097, 9000, 33, 0, 2],
              "reversed_ids": [8192, 7000], "runs32": [32 * 700 + 5], "runs33": [33 * 300],
-             "hi_ties": [40000]}[case]
+             "hi_ties": [40000], "prefix_ties": [50000, 7]}[case]
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     total = int(off[-1])
     key_bits = 128
@@ -105,6 +105,10 @@ def test_sort_keys_matches_stable_sort(hc, case):
     if case == "hi_ties":          # short runs of equal high words, some equal keys
         hi = hi[rng.integers(0, total // 3, size=total)].copy()
         lo[rng.random(total) < 0.3] = np.uint64(5)
+    if case == "prefix_ties":      # equal top 56 bits, differing low bytes of the high word
+        top = hi[rng.integers(0, total // 4, size=total)] & np.uint64(0xFFFFFFFFFFFFFF00)
+        hi = top | rng.integers(0, 4, size=total, dtype=np.uint64)
+        lo[rng.random(total) < 0.5] = np.uint64(9)
     ids = np.arange(total, dtype=np.uint32)
     if case == "reversed_ids":
         ids = ids[::-1].copy()
