@@ -86,6 +86,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms, world, device):
+    """The timed region's length on the slowest rank (ms).  The only collective
+    of the benchmark: the ranks' query batches are independent, so nothing is
+    exchanged on the data path."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ms_per_step, nq_per_rank, world):
+    """Whole-job queries/s: every rank answers its own nq queries per step
+    (weak scaling), and the step lasts as long as the slowest rank's."""
+    return world * nq_per_rank / (ms_per_step / 1000.0)
+
+
 def workload_name(a):
     return ("plain Hypercurves at scale: N=%d x %d-d %s, 8 curves x 16 dims, Q=%d, p=%d, k=%d; "
             "step = index build + query batch" % (a.n_db, 128, "uint8" if a.dtype == "u8"
@@ -328,11 +346,8 @@ def run_hc(a):
     build_ms = [e[0].elapsed_time(e[1]) for e in events]
     query_ms = [e[1].elapsed_time(e[2]) for e in events]
     step_ms = [e[0].elapsed_time(e[2]) for e in events]
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / a.steps
-    value = world * a.nq / (ms_per_step / 1000.0)
+    ms_per_step = max_over_ranks(total_ms, world, "cuda") / a.steps
+    value = job_throughput(ms_per_step, a.nq, world)
 
     if rank != 0:
         if world > 1:
