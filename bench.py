@@ -51,11 +51,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hc", "reference"], default="hc")
-    ap.add_argument("--workload", choices=["scale", "uneven", "learned", "serve"],
+    ap.add_argument("--workload", choices=["scale", "uneven", "learned", "serve", "partitions"],
                     default="scale",
                     help="scale: the headline (build + query at N=10M); uneven: 64 indexes in "
                          "one persistent launch; learned: learned probe depth; serve: online "
-                         "serving under fluctuating load")
+                         "serving under fluctuating load; partitions: partitioned "
+                         "Hypercurves, Optimist/Pessimist slack")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--serve-n", type=int, default=50_000_000)
     ap.add_argument("--train-queries", type=int, default=1_000_000)
@@ -459,6 +460,9 @@ def main():
     if a.workload == "serve":
         from bench_workloads import run_serve
         return run_serve(a)
+    if a.workload == "partitions":
+        from bench_workloads import run_partitions
+        return run_partitions(a)
     return run_hc(a)
 
 

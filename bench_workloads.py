@@ -13,8 +13,16 @@ serve    N = 50M uint8 resident, Poisson arrivals whose rate follows seeded
          on/off bursts times a sinusoid between 10k and 500k queries/s, k = 10,
          requests with p = 0 (learned depth, fixed-depth fallback), HBM-budget
          admission: p50/p99 latency and sustained queries/s.
+partitions
+         partitioned Hypercurves on one GPU (Sec. 4): N = 10M uint8 split into
+         ell in {1, 2, 4, 8, 16, 32} in-HBM partitions, sequential depth
+         Phi = 128, local depth phi from the Optimist (slack 0) and Pessimist
+         (smallest slack with Eq. 6 below 2%) settings: build and query time,
+         recall@10, and how often the answer equals / is no worse than the
+         sequential one.
 """
 import json
+from fractions import Fraction
 import math
 import os
 import statistics
@@ -309,4 +317,67 @@ def run_serve(a):
                       "mean_batch_queries": st["queries_done"] / max(1, st["batches_done"]),
                       "setup_s": setup_s}})
     mlp.free()
+    return 0
+
+
+# -------------------------------------------------------------- partitions
+def run_partitions(a):
+    import torch
+    from paper_1209_0410_gb300 import datagen, hc, learned, partition
+    torch.cuda.set_device(0)
+    n, nq, Phi, k = a.n_db, a.nq, a.p, a.k
+    db = datagen.make_db(n, 128, seed=datagen.SEED_DB)
+    q = datagen.make_queries(db, nq, seed=datagen.SEED_QUERIES)
+    tdb = torch.from_numpy(db).cuda()
+    tq = torch.from_numpy(q).cuda()
+    stream = torch.cuda.current_stream()
+    rs = min(2000, nq)
+    _, tdist = hc.hc_bruteforce(tdb, tq[:rs], 10)
+    reps = max(3, min(a.steps, 10))
+    seq_ids = seq_dist = None
+    rows = []
+    for ell in (1, 2, 4, 8, 16, 32):
+        e0, e1 = _events()
+        hc.hc_build(tdb, 8, 16, partitions=ell).free()      # warm the pool
+        e0.record(stream)
+        idx = hc.hc_build(tdb, 8, 16, partitions=ell)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        build_ms = e0.elapsed_time(e1)
+        settings = [("optimist", Fraction(0))]
+        if ell > 1:
+            settings.append(("pessimist", partition.pessimist_slack(Phi, ell)))
+        for name, slack in settings:
+            phi = partition.slack_depth(Phi, ell, slack)
+            ids, dist = hc.hc_query(idx, tq, k, phi)
+            e0, e1 = _events()
+            e0.record(stream)
+            for _ in range(reps):
+                hc.hc_query(idx, tq, k, phi, ids, dist)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            if seq_ids is None:
+                seq_ids, seq_dist = ids.clone(), dist.clone()
+            row = {"ell": ell, "setting": name, "slack": float(slack), "phi": phi,
+                   "bound_eq6": partition.equiv_bound(Phi, ell, phi) if ell > 1 else 0.0,
+                   "build_ms": build_ms, "query_ms": ms, "qps": nq / (ms / 1e3),
+                   "window_rows_per_query": 2 * phi * ell * 8,
+                   "recall_at_10": learned.recall_at_10(ids[:rs], dist[:rs], tdist),
+                   "equal_to_sequential": learned.agreement(ids, seq_ids),
+                   "no_worse_than_sequential": float(
+                       (dist <= seq_dist).all(dim=1).double().mean().item())}
+            rows.append(row)
+        idx.free()
+    ref = [r for r in rows if r["ell"] == 8 and r["setting"] == "pessimist"][0]
+    _line({"metric": "queries/s, partitioned Hypercurves (8 in-HBM partitions, Pessimist "
+                     "slack), 10M x 128 uint8", "value": ref["qps"], "unit": "queries/s",
+           "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": ref["query_ms"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+           "data": "synthetic: seeded 64-cluster Gaussian mixture (SIFT stand-in)",
+           "config": {"workload": "partitioned Hypercurves: N=%d, Q=%d, sequential depth "
+                                  "Phi=%d per side, k=%d, ell in {1..32} contiguous "
+                                  "partitions, Optimist / Pessimist slack" % (n, nq, Phi, k),
+                      "l2": "inputs larger than L2 (database %.2f GB)" % (n * 128 / 1e9),
+                      "recall_sample_queries": rs, "sweep": rows}})
     return 0

@@ -209,7 +209,8 @@ def test_query_u8_other_shapes(hc, d, curves, m, k, p):
     idx.free()
 
 
-@pytest.mark.parametrize("parts,scheme_p", [(2, 64), (3, 20), (8, 10), (5, 100000)])
+@pytest.mark.parametrize("parts,scheme_p", [(2, 64), (3, 20), (8, 10), (5, 100000), (32, 13),
+                                             (32, 4)])
 def test_query_partitioned_bit_exact(hc, parts, scheme_p):
     n, nq, k = 24000, 150, 10
     db, q = make_case(n, nq, seed=parts)
