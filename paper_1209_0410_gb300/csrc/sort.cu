@@ -13,9 +13,9 @@
 // Per pass, three kernels, none of which waits on another block:
 //   hist    one 4096-record tile per block: digit counts -> counts[seg][digit][tile]
 //   scan    one block per (segment, digit): exclusive scan over the tiles
-//   scatter one tile per block: stable in-tile ranking with __match_any_sync
-//           per warp round, a shared-memory reorder by digit, then coalesced
-//           runs to global memory.
+//   scatter one tile per block: stable in-tile ranking (warp-level multisplit
+//           by ballots plus per-warp digit counts), a shared-memory reorder
+//           by digit, then coalesced runs to global memory.
 #include <algorithm>
 #include <cstring>
 
@@ -28,8 +28,7 @@ namespace {
 constexpr int kThreads = 256;                 // histogram / scan / gather blocks
 constexpr int kWarps = kThreads / 32;
 constexpr int kTile = 4096;                    // records per tile
-// scatter blocks: 16 warps of 256 consecutive records each (8 per lane), so
-// that the serial in-warp ranking chain is 8 rounds long
+// scatter blocks: 16 warps of 256 consecutive records each (8 rounds of 32)
 constexpr int kSThreads = 512;
 constexpr int kSWarps = kSThreads / 32;
 constexpr int kIpt = kTile / kSThreads;        // 8 records per thread
@@ -144,79 +143,43 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const SegInfo* __restric
     }
 }
 
-// One scatter tile in shared memory: the words and positions of the tile
-// (padded so that blocked and striped accesses are free of bank conflicts),
-// the per-thread nibble counters, and per-digit bases.
+// One scatter tile in shared memory: the words and positions of the tile in
+// digit order (padded against bank conflicts on the striped read-out), the
+// per-warp digit counts (then their digit-major exclusive prefixes), and the
+// global destination base per digit.
 constexpr int kPadW = kTile + kTile / 16;   // one spare word slot per 16
 constexpr int kPadP = kTile + kTile / 32;   // one spare position slot per 32
+constexpr int kHistStride = 257;            // warps' count rows, odd stride
 __device__ __forceinline__ int padw(int i) { return i + (i >> 4); }
 __device__ __forceinline__ int padp(int i) { return i + (i >> 5); }
 
 struct ScatterSmem {
     uint64_t w[kPadW];
     uint32_t p[kPadP];
-    uint16_t cnt[16][kSThreads];   // nibble counts, then exclusive bases
+    uint32_t hist[kSWarps * kHistStride];   // [warp][digit]
     uint64_t gbase[256];
-    uint16_t dstart[256];
     uint32_t warp_sums[kSWarps];
 };
 
-// Stable counting sort of the tile by a 4-bit slice of the digit: each thread
-// owns records 8t..8t+7 (in registers), counts its nibbles in 4-bit fields of
-// two 32-bit registers (buckets 0-7, 8-15), the 16 x 512 counts are scanned
-// bucket-major (each thread scans a 32-byte slice with two 16-byte accesses),
-// and each record lands at its bucket base + its rank among the thread's
-// earlier records of that bucket.
-__device__ __forceinline__ void nibble_pass(ScatterSmem& sm, const uint64_t (&w)[kIpt],
-                                            const uint32_t (&p)[kIpt],
-                                            const uint32_t (&dg)[kIpt], int nshift) {
-    const int t = threadIdx.x;
-    uint32_t c0 = 0, c1 = 0;
-#pragma unroll
-    for (int j = 0; j < kIpt; ++j) {
-        const uint32_t b = (dg[j] >> nshift) & 0xF;
-        const uint32_t inc = 1u << (4 * (b & 7));
-        c0 += b < 8 ? inc : 0u;
-        c1 += b < 8 ? 0u : inc;
-    }
+// Lanes of the warp whose 8-bit digit equals this lane's (warp-level
+// multisplit by ballots, one per digit bit).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+    uint32_t peers = 0xffffffffu;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-        sm.cnt[b][t] = (uint16_t)((c0 >> (4 * b)) & 0xF);
-        sm.cnt[b + 8][t] = (uint16_t)((c1 >> (4 * b)) & 0xF);
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
     }
-    __syncthreads();
-    // bucket-major exclusive scan: thread t owns entries [16t, 16t + 16)
-    uint4* slice = reinterpret_cast<uint4*>(&sm.cnt[0][0]) + 2 * t;
-    const uint4 s0 = slice[0], s1 = slice[1];
-    const uint32_t words[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-    uint32_t sum = 0;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) sum += (words[e] & 0xFFFFu) + (words[e] >> 16);
-    uint32_t run = block_exclusive_scan<kSWarps>(sum, sm.warp_sums);
-    uint32_t out[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const uint32_t a = words[e] & 0xFFFFu, b = words[e] >> 16;
-        out[e] = run | ((run + a) << 16);
-        run += a + b;
-    }
-    slice[0] = make_uint4(out[0], out[1], out[2], out[3]);
-    slice[1] = make_uint4(out[4], out[5], out[6], out[7]);
-    __syncthreads();
-    uint32_t s0c = 0, s1c = 0;   // records of the thread seen so far, per bucket
-#pragma unroll
-    for (int j = 0; j < kIpt; ++j) {
-        const uint32_t b = (dg[j] >> nshift) & 0xF;
-        const uint32_t sh = 4 * (b & 7);
-        const uint32_t seen = ((b < 8 ? s0c : s1c) >> sh) & 0xF;
-        const uint32_t rank = sm.cnt[b][t] + seen;
-        if (b < 8) s0c += 1u << sh; else s1c += 1u << sh;
-        sm.w[padw(rank)] = w[j];
-        sm.p[padp(rank)] = p[j];
-    }
-    __syncthreads();
+    return peers;
 }
 
+// Tile ranking: warp w owns records [256 w, 256 w + 256), lane l of round r
+// holds record 256 w + 32 r + l (coalesced loads).  Each round ranks its 32
+// records among the warp's earlier records of the same digit (ballot peers +
+// the warp's running digit counts); the digit-major scan of the 16 x 256
+// counts then gives every record its place in the digit-sorted tile, stable
+// in record order.  Records past the tile's end carry digit 255 and sort last.
 __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
     const uint64_t* __restrict__ wsrc, const uint32_t* __restrict__ psrc,
     uint64_t* __restrict__ wdst, uint32_t* __restrict__ pdst, int shift, uint32_t nseg,
@@ -229,55 +192,74 @@ __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
     uint32_t seg, lt, count;
     uint64_t start;
     tile_of(nseg, segs, si, seg, lt, start, count);
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
 
-    // blocked records; past the tile's end: digit 255 and last in order
     uint64_t w[kIpt];
     uint32_t p[kIpt];
 #pragma unroll
-    for (int j = 0; j < kIpt; ++j) {
-        const uint32_t i = (uint32_t)t * kIpt + j;
+    for (int r = 0; r < kIpt; ++r) {
+        const uint32_t i = (uint32_t)warp * kWarpItems + (uint32_t)r * 32 + (uint32_t)lane;
         const bool valid = i < count;
-        w[j] = valid ? __ldg(wsrc + start + i) : (0xFFull << shift);
-        p[j] = valid ? (psrc ? __ldg(psrc + start + i) : (uint32_t)(start + i)) : 0u;
+        w[r] = valid ? __ldg(wsrc + start + i) : (0xFFull << shift);
+        p[r] = valid ? (psrc ? __ldg(psrc + start + i) : (uint32_t)(start + i)) : 0u;
     }
-    // the digit is bits [shift, shift + 8) of the word: low nibble, then high
-    uint32_t dg[kIpt];
+    for (int i = t; i < kSWarps * kHistStride; i += kSThreads) sm.hist[i] = 0;
+    __syncthreads();
+
+    uint32_t* wh = sm.hist + warp * kHistStride;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t rank[kIpt];
 #pragma unroll
-    for (int j = 0; j < kIpt; ++j) dg[j] = (uint32_t)(w[j] >> shift) & 0xFFu;
-    nibble_pass(sm, w, p, dg, 0);
-#pragma unroll
-    for (int j = 0; j < kIpt; ++j) {
-        const int i = t * kIpt + j;
-        w[j] = sm.w[padw(i)];
-        p[j] = sm.p[padp(i)];
-        dg[j] = (uint32_t)(w[j] >> shift) & 0xFFu;
+    for (int r = 0; r < kIpt; ++r) {
+        const uint32_t d = (uint32_t)(w[r] >> shift) & 0xFFu;
+        const uint32_t peers = digit_peers(d);
+        const uint32_t before = wh[d];
+        rank[r] = before + __popc(peers & lt_mask);
+        __syncwarp();
+        if ((peers & lt_mask) == 0) wh[d] = before + __popc(peers);
+        __syncwarp();
     }
     __syncthreads();
-    nibble_pass(sm, w, p, dg, 4);
 
-    // where each digit's run starts in the sorted tile
-    for (uint32_t i = t; i < count; i += kSThreads) {
-        const uint32_t d = (uint32_t)(sm.w[padw(i)] >> shift) & 0xFFu;
-        if (i == 0 || ((uint32_t)(sm.w[padw(i - 1)] >> shift) & 0xFFu) != d)
-            sm.dstart[d] = (uint16_t)i;
+    // digit-major exclusive scan of hist[warp][digit]: thread t owns digit
+    // t / 2, warps 8 (t % 2) .. 8 (t % 2) + 7
+    {
+        const uint32_t d = (uint32_t)t >> 1, w0 = ((uint32_t)t & 1u) * 8;
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            v[j] = sm.hist[(w0 + j) * kHistStride + d];
+            sum += v[j];
+        }
+        uint32_t run = block_exclusive_scan<kSWarps>(sum, sm.warp_sums);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            sm.hist[(w0 + j) * kHistStride + d] = run;
+            run += v[j];
+        }
     }
     {
-        // threads 0..255 own one digit each; the rest add zeros to the scan
+        // global destination of sorted-tile slot i with digit d: gbase[d] + i
         const uint32_t dg = t;
         const bool own = dg < 256;
         const uint32_t seg_prefix = block_exclusive_scan<kSWarps>(
             own ? __ldg(totals + (uint64_t)seg * 256 + dg) : 0u, sm.warp_sums);
         if (own) {
             const uint32_t before = __ldg(counts + si.cnt_base + (uint64_t)dg * si.ntiles + lt);
-            sm.gbase[dg] = si.start + seg_prefix + before;
+            sm.gbase[dg] = si.start + seg_prefix + before - sm.hist[dg];
         }
+    }
+#pragma unroll
+    for (int r = 0; r < kIpt; ++r) {
+        const uint32_t d = (uint32_t)(w[r] >> shift) & 0xFFu;
+        const uint32_t slot = wh[d] + rank[r];
+        sm.w[padw(slot)] = w[r];
+        sm.p[padp(slot)] = p[r];
     }
     __syncthreads();
     for (uint32_t i = t; i < count; i += kSThreads) {
         const uint64_t v = sm.w[padw(i)];
-        const uint32_t d = (uint32_t)(v >> shift) & 0xFFu;
-        const uint64_t g = sm.gbase[d] + (i - sm.dstart[d]);
+        const uint64_t g = sm.gbase[(uint32_t)(v >> shift) & 0xFFu] + i;
         wdst[g] = v;
         pdst[g] = sm.p[padp(i)];
     }
