@@ -98,8 +98,10 @@ typedef struct {
  *   out      receives the new index (owned by the library; free with hc_free).
  * The library allocates the index arrays (20 bytes per row and curve) and,
  * during the call, scratch of about 44 bytes per row and curve; HC_ERR_OOM
- * if that fails.  Asynchronous on cuda_stream; the index may be used by
- * later work on the same stream (or after synchronising).
+ * if that fails.  Work is queued on cuda_stream; the call waits on that stream
+ * once, after the sort, to read the sort's device status (a run of equal
+ * 56-bit key prefixes longer than 32 makes it sort again by every key byte).
+ * The index may be used by later work on the same stream.
  */
 HC_API int hc_build(const void* db_dev, const hc_build_params* params, void* cuda_stream,
                     hc_index** out);
@@ -211,7 +213,7 @@ HC_API int hc_hilbert_keys(const void* x_dev, hc_dtype dtype, uint64_t count, ui
  *                            total < 2^32
  *   key_bits                 significant low bits of every key (1..128);
  *                            digits above them are taken as zero and skipped
- * Allocates scratch of 36 bytes per record for the call; synchronises
+ * Allocates scratch of about 36 bytes per record for the call; synchronises
  * cuda_stream before returning (the scratch is freed).
  */
 HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
@@ -296,6 +298,8 @@ typedef struct hc_multi_plan hc_multi_plan;
  * tables and, with use_graph, captures the launch in a CUDA graph.  The
  * plan refers to the jobs' buffers: new queries written into the same
  * q_dev buffers are answered by the next hc_multi_run.  cfg may be NULL.
+ * The tables are copied synchronously (blocking copies); cuda_stream is not
+ * used by this call.
  */
 HC_API int hc_multi_plan_create(const hc_multi_job* jobs, uint32_t njobs,
                                 const hc_multi_config* cfg, void* cuda_stream,

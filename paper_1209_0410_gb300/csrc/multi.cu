@@ -247,7 +247,7 @@ HC_API int hc_multi_plan_create(const hc_multi_job* jobs, uint32_t njobs,
     P->cfg = cfg;
     P->njobs = njobs;
     P->ntasks = (uint32_t)sorted.size();
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    (void)cuda_stream;   // the tables are copied synchronously
     bool ok = !alloc_should_fail() &&
               cudaMalloc(&P->jobs_dev, sizeof(MultiJob) * njobs) == cudaSuccess &&
               cudaMalloc(&P->tasks_dev, sizeof(MultiTask) * std::max<size_t>(1, sorted.size())) ==
@@ -295,7 +295,6 @@ HC_API int hc_multi_plan_create(const hc_multi_job* jobs, uint32_t njobs,
             return rc;
         }
     }
-    (void)s;
     *out = P;
     return HC_OK;
 }
