@@ -233,4 +233,158 @@ __device__ __forceinline__ void search_lists(const IndexView& ix, const uint8_t*
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Staged form of the window walk for rows of at most 128 bytes (one 16-byte
+// vector per lane of a row group, LPR <= 8): the rows of the next 32-entry
+// step are copied into a per-warp shared-memory ring with cp.async (no
+// registers held while they are in flight) while the current step's rows are
+// reduced, and the step after that has its ids loaded.  The steps run over
+// all windows of the query back to back, so the copies do not drain at
+// window ends.  Waits are the hardware's cp.async group waits.
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// window [lo, hi) of list L around position pos_w[L]
+__device__ __forceinline__ void window_of(const IndexView& ix, const uint32_t* pos_w,
+                                          uint32_t depth, uint32_t L, uint32_t& lo,
+                                          uint32_t& hi) {
+    const uint32_t n = (uint32_t)(ix.list_off[L + 1] - ix.list_off[L]);
+    const uint32_t pos = pos_w[L];
+    lo = pos > depth ? pos - depth : 0u;
+    hi = (uint64_t)pos + depth < (uint64_t)n ? pos + depth : n;
+}
+
+// the step after (L, base) in the walk over lists L0, L0 + Lstep, ...;
+// false when the walk is over
+__device__ __forceinline__ bool next_step(const IndexView& ix, const uint32_t* pos_w,
+                                          uint32_t depth, uint32_t Lstep, uint32_t& L,
+                                          uint32_t& base, uint32_t& hi) {
+    base += 32;
+    while (base >= hi) {
+        L += Lstep;
+        if (L >= ix.lists) return false;
+        window_of(ix, pos_w, depth, L, base, hi);
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t step_ids(const IndexView& ix, uint32_t L, uint32_t base,
+                                             uint32_t hi, int lane) {
+    const uint32_t e = base + (uint32_t)lane;
+    return e < hi ? __ldg(ix.ids + ix.list_off[L] + e) : 0u;
+}
+
+// copies of one step: lane (c = lane % 8, g = lane / 8) moves vector c of
+// rows g, g + 4, ..., g + 28 (rows past cnt and vectors past the row are
+// skipped)
+__device__ __forceinline__ void issue_step(const uint8_t* __restrict__ db, uint32_t row_bytes,
+                                           uint32_t sbuf, uint32_t id, uint32_t cnt, int lane) {
+    const uint32_t c = (uint32_t)lane & 7u, g = (uint32_t)lane >> 3;
+    const bool colok = c < (row_bytes >> 4);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const uint32_t r = g + 4u * (uint32_t)t;
+        const uint32_t rid = __shfl_sync(0xffffffffu, id, (int)r);
+        if (colok && r < cnt)
+            cp_async16(sbuf + r * row_bytes + c * 16, db + (size_t)rid * row_bytes + c * 16);
+    }
+}
+
+// chunk_candidates_n over rows staged in shared memory (LPR <= 8, so one
+// candidate per lane)
+template <bool F32, int LPR>
+__device__ __forceinline__ uint64_t staged_candidates(const uint8_t* sbuf, uint32_t row_bytes,
+                                                      uint4 qv0, uint32_t id, uint32_t cnt,
+                                                      int lane) {
+    static_assert(LPR <= 8, "staged rows are read one vector per lane");
+    using Acc = typename std::conditional<F32, float, uint32_t>::type;
+    constexpr int RPI = 32 / LPR;
+    const uint32_t s = (uint32_t)lane % LPR, g = (uint32_t)lane / LPR;
+    const bool colok = s < (row_bytes >> 4);
+    Acc part[LPR];
+#pragma unroll
+    for (int j = 0; j < LPR; ++j) {
+        const uint32_t r = (uint32_t)j * RPI + g;
+        const uint4 rv = colok ? *reinterpret_cast<const uint4*>(sbuf + r * row_bytes + s * 16)
+                               : make_uint4(0, 0, 0, 0);
+        part[j] = acc_vec(rv, qv0, Acc(0));
+    }
+    const Acc dsum = reduce_scatter<LPR>(part, s);
+    const uint32_t r = s * RPI + g;
+    const uint32_t cid = __shfl_sync(0xffffffffu, id, (int)r);
+    return r < cnt ? ((uint64_t)dist_bits(dsum) << 32) | cid : kEmpty;
+}
+
+template <bool F32, int LPR, int KR>
+__device__ __forceinline__ void search_lists_staged(const IndexView& ix, const uint8_t* qrow,
+                                                    uint32_t depth, uint32_t k, uint32_t L0,
+                                                    uint32_t Lstep, uint32_t* pos_w,
+                                                    uint8_t* ring, WarpTopK<KR>& top, int lane,
+                                                    const int64_t* pos_in = nullptr) {
+    if (pos_in) {
+        for (uint32_t L = L0 + (uint32_t)lane * Lstep; L < ix.lists; L += 32 * Lstep)
+            pos_w[L] = (uint32_t)__ldg(pos_in + L);
+        __syncwarp();
+    } else {
+        query_positions(ix, qrow, pos_w, lane, L0, Lstep);
+    }
+    const uint32_t s = (uint32_t)lane % LPR;
+    const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
+    const uint8_t* db = static_cast<const uint8_t*>(ix.db);
+    const uint32_t stage_bytes = 32 * ix.row_bytes;
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+
+    // first non-empty window: step A
+    uint32_t aL = L0, abase = 0, ahi = 0;
+    for (; aL < ix.lists; aL += Lstep) {
+        window_of(ix, pos_w, depth, aL, abase, ahi);
+        if (abase < ahi) break;
+    }
+    if (aL >= ix.lists) return;
+    uint32_t aid = step_ids(ix, aL, abase, ahi, lane);
+    issue_step(db, ix.row_bytes, ring_s, aid, min(32u, ahi - abase), lane);
+    cp_async_commit();
+    // step B after A
+    uint32_t bL = aL, bbase = abase, bhi = ahi;
+    bool hb = next_step(ix, pos_w, depth, Lstep, bL, bbase, bhi);
+    uint32_t bid = hb ? step_ids(ix, bL, bbase, bhi, lane) : 0u;
+    uint32_t st = 0;
+    while (true) {
+        if (hb)
+            issue_step(db, ix.row_bytes, ring_s + (st ^ 1u) * stage_bytes, bid,
+                       min(32u, bhi - bbase), lane);
+        cp_async_commit();
+        // step C after B: its ids
+        uint32_t cL = bL, cbase = bbase, chi = bhi;
+        const bool hc = hb && next_step(ix, pos_w, depth, Lstep, cL, cbase, chi);
+        const uint32_t cid = hc ? step_ids(ix, cL, cbase, chi, lane) : 0u;
+        cp_async_wait<1>();   // step A has landed
+        __syncwarp();
+        top.offer(staged_candidates<F32, LPR>(ring + st * stage_bytes, ix.row_bytes, qv0, aid,
+                                              min(32u, ahi - abase), lane),
+                  k, lane);
+        __syncwarp();         // every lane is done with stage st before it is refilled
+        if (!hb) break;
+        aid = bid;
+        abase = bbase;
+        ahi = bhi;
+        bL = cL;
+        bbase = cbase;
+        bhi = chi;
+        bid = cid;
+        hb = hc;
+        st ^= 1u;
+    }
+    cp_async_wait<0>();
+}
+
 }  // namespace hc

@@ -8,9 +8,13 @@
 //   K4  for every list, the window [max(0,pos-p), min(n,pos+p)) is walked 32
 //       entries at a time: the 32 ids are one coalesced load, then each row
 //       is read as 16-byte vectors by LPR lanes (LPR = 8 for 128-byte uint8
-//       rows: four rows per warp instruction, up to eight instructions in
-//       flight per lane); uint8 partial distances use vabsdiffu4 + dp4a
-//       (exact in 32-bit integers), float32 use fma;
+//       rows: four rows per warp instruction).  Rows of at most 128 bytes are
+//       staged: the next step's rows are copied into a two-step per-warp
+//       shared-memory ring with cp.async while the current step is reduced,
+//       across window ends, so the bytes in flight are bounded by shared
+//       memory instead of registers; wider rows are gathered into registers,
+//       eight 16-byte loads in flight per lane.  uint8 partial distances use
+//       vabsdiffu4 + dp4a (exact in 32-bit integers), float32 use fma;
 //       a reduce-scatter over the LPR lanes leaves lane l with the distance
 //       of one row of the 32 (LPR-1 shuffles for LPR partial sums);
 //   K5/K6 the 32 packed (distance, id) candidates are offered to one running
@@ -45,9 +49,11 @@ struct QueryArgs {
                                  // (3 x 8 warps: best at p = 128 and 512 on GB300)
 #endif
 
-template <bool F32, int LPR, int KR>
+// STAGED: rows of at most 128 bytes go through a two-step cp.async ring in
+// shared memory (kQWarps x 2 x 32 rows after the positions)
+template <bool F32, int LPR, int KR, bool STAGED>
 __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kernel(QueryArgs a) {
-    extern __shared__ uint32_t s_pos[];  // kQWarps x lists
+    extern __shared__ __align__(16) uint32_t s_pos[];  // kQWarps x lists, then the rings
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t qi = blockIdx.x * kQWarps + warp;
     if (qi >= a.nq) return;
@@ -56,8 +62,16 @@ __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kerne
     const uint32_t depth = a.p_query ? __ldg(a.p_query + qi) : a.p;
     WarpTopK<KR> top;
     top.init();
-    search_lists<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, top, lane,
-                               a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
+    if constexpr (STAGED) {
+        uint8_t* ring = reinterpret_cast<uint8_t*>(s_pos + kQWarps * ix.lists) +
+                        (size_t)warp * 64 * ix.row_bytes;
+        search_lists_staged<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists,
+                                          ring, top, lane,
+                                          a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
+    } else {
+        search_lists<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, top,
+                                   lane, a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
+    }
     top.template store<F32>(a.k, lane, a.out_ids + (size_t)qi * a.k,
                             static_cast<uint32_t*>(a.out_dist) + (size_t)qi * a.k);
 }
@@ -131,8 +145,20 @@ template <bool F32, int LPR, int KR>
 struct QueryLaunch {
     static cudaError_t run(const QueryArgs& a, cudaStream_t s) {
         const unsigned blocks = (a.nq + kQWarps - 1) / kQWarps;
-        const size_t smem = sizeof(uint32_t) * kQWarps * a.ix.lists;
-        query_kernel<F32, LPR, KR><<<blocks, kQWarps * 32, smem, s>>>(a);
+        const size_t pos_bytes = sizeof(uint32_t) * kQWarps * a.ix.lists;
+        if constexpr (LPR <= 8) {
+            if (a.ix.row_bytes <= 128) {
+                const size_t smem = pos_bytes + (size_t)kQWarps * 64 * a.ix.row_bytes;
+                cudaError_t e = cudaFuncSetAttribute(query_kernel<F32, LPR, KR, true>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
+                if (e != cudaSuccess) return e;
+                query_kernel<F32, LPR, KR, true><<<blocks, kQWarps * 32, smem, s>>>(a);
+                count_launches(1);
+                return cudaGetLastError();
+            }
+        }
+        query_kernel<F32, LPR, KR, false><<<blocks, kQWarps * 32, pos_bytes, s>>>(a);
         count_launches(1);
         return cudaGetLastError();
     }
