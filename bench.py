@@ -213,7 +213,8 @@ class ClockSampler:
 def algorithmic_query_bytes(hc, idx, q_dev, p, k, row_bytes):
     """Bytes the method itself must move for one query launch (per query:
     window ids 4 B + window rows, the global binary-search probes beyond 12
-    cached levels at 16 B, the query row and k (id, distance) results)."""
+    cached levels at 8 B (the high key word; the low word is needed only on
+    the rare ties), the query row and k (id, distance) results)."""
     import torch
     pos = hc.hc_query_positions(idx, q_dev)
     _, off = hc.hc_index_describe(idx)
@@ -223,7 +224,7 @@ def algorithmic_query_bytes(hc, idx, q_dev, p, k, row_bytes):
     windows = int((hi - lo).clamp(min=0).sum().item())
     nq, lists = pos.shape
     lg = sum(max(0, int(n).bit_length() - 12) for n in (off[1:] - off[:-1]).tolist())
-    return windows * (row_bytes + 4) + nq * (lg * 16 + row_bytes + k * 8), windows
+    return windows * (row_bytes + 4) + nq * (lg * 8 + row_bytes + k * 8), windows
 
 
 def recall_at_10(ids, dist, true_dist):
@@ -377,7 +378,7 @@ def run_hc(a):
     cfg = {"workload": workload_name(a), "n_db": a.n_db, "nq": a.nq, "p": a.p, "k": a.k,
            "curves": 8, "dims_per_curve": 16, "partitions": 1,
            "l2": "inputs larger than L2 (database %.2f GB, index %.2f GB vs 129 MB L2)"
-                 % (a.n_db * row_bytes / 1e9, a.n_db * 8 * 20 / 1e9),
+                 % (a.n_db * row_bytes / 1e9, a.n_db * 8 * 12 / 1e9),
            "build_ms": statistics.mean(build_ms), "query_ms": q_ms,
            "query_only_qps": a.nq / (q_ms / 1000.0),
            "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)),

@@ -96,8 +96,11 @@ typedef struct {
  *            NOT copied: the index keeps the pointer, so the caller keeps the
  *            buffer alive and unchanged until hc_free.
  *   out      receives the new index (owned by the library; free with hc_free).
- * The library allocates the index arrays (20 bytes per row and curve) and,
- * during the call, scratch of about 44 bytes per row and curve; HC_ERR_OOM
+ * The library allocates the index arrays (12 bytes per row and curve for
+ * 16-coordinate curves, whose lists keep the high key word and the id; 20
+ * bytes otherwise) and, during the call, scratch of about 25 bytes per row
+ * and curve (33 when low words are kept; more if a run of over 32 equal
+ * 56-bit key prefixes makes it sort by every key byte); HC_ERR_OOM
  * if that fails.  Work is queued on cuda_stream; the call waits on that stream
  * once, after the sort, to read the sort's device status (a run of equal
  * 56-bit key prefixes longer than 32 makes it sort again by every key byte).
@@ -174,7 +177,9 @@ typedef struct {
     uint32_t d, curves, dims_per_curve, partitions, lists;
     hc_dtype dtype;
     const uint64_t* keys_hi_dev;  /* lists concatenated, list L = part*curves + c */
-    const uint64_t* keys_lo_dev;  /* low 64 bits of each key */
+    const uint64_t* keys_lo_dev;  /* low 64 bits of each key; NULL when the index keeps
+                                     high words only (dims_per_curve = 16: a low word is
+                                     recomputed from its row when high words tie) */
     const uint32_t* ids_dev;      /* row id of each entry */
     const void* db_dev;
 } hc_index_info;
@@ -185,7 +190,8 @@ HC_API int hc_index_describe(const hc_index* idx, hc_index_info* info, uint64_t*
 
 /* hc_index_copy_lists -- copies the sorted lists (all lists concatenated,
  * list_off order) into caller-owned device buffers of total = n * curves
- * entries each.  Asynchronous on cuda_stream; no allocation. */
+ * entries each; low key words the index does not keep are recomputed from
+ * the rows.  Asynchronous on cuda_stream; no allocation. */
 HC_API int hc_index_copy_lists(const hc_index* idx, uint64_t* keys_hi_dev, uint64_t* keys_lo_dev,
                                uint32_t* ids_dev, void* cuda_stream);
 

@@ -158,8 +158,13 @@ int build_index(hc_index* x, cudaStream_t s) {
     if ((rc = status_of(upload_small(x->list_off_dev, x->list_off.data(),
                                      sizeof(uint64_t) * (x->lists + 1), s))))
         return rc;
+    // 16-coordinate keys: the high word holds 64 key bits and ties of it are
+    // rare, so the index keeps high words only and recomputes a low word from
+    // its row when a tie needs it (12 instead of 20 bytes per entry)
+    const bool keep_lo = P.dims_per_curve < 16;
     if ((rc = dev_alloc_async((void**)&x->keys_hi, sizeof(uint64_t) * total, s))) return rc;
-    if ((rc = dev_alloc_async((void**)&x->keys_lo, sizeof(uint64_t) * total, s))) return rc;
+    if (keep_lo && (rc = dev_alloc_async((void**)&x->keys_lo, sizeof(uint64_t) * total, s)))
+        return rc;
     if ((rc = dev_alloc_async((void**)&x->ids, sizeof(uint32_t) * total, s))) return rc;
 
     SortProblem sp;
@@ -177,12 +182,12 @@ int build_index(hc_index* x, cudaStream_t s) {
     for (uint32_t L = 0; L < x->lists; ++L)
         id_base[L] = partition_start(L / P.curves, P.n, parts);
     const size_t sort_bytes = sort_scratch_bytes(sp);
-    const size_t key_bytes = ((sizeof(uint64_t) * 2 * total) + 255) & ~(size_t)255;
+    const size_t key_bytes = ((sizeof(uint64_t) * (keep_lo ? 2 : 1) * total) + 255) & ~(size_t)255;
     const size_t base_bytes = (sizeof(uint64_t) * x->lists + 255) & ~(size_t)255;
     void* scratch = nullptr;
     if ((rc = dev_alloc_async(&scratch, key_bytes + base_bytes + sort_bytes, s))) return rc;
     uint64_t* hi0 = static_cast<uint64_t*>(scratch);
-    uint64_t* lo0 = hi0 + total;
+    uint64_t* lo0 = keep_lo ? hi0 + total : nullptr;
     uint64_t* id_base_dev = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + key_bytes);
     void* sort_scratch = static_cast<char*>(scratch) + key_bytes + base_bytes;
 
@@ -196,7 +201,28 @@ int build_index(hc_index* x, cudaStream_t s) {
         sp.lo = lo0;
         sp.ids = nullptr;
         sp.id_base_dev = id_base_dev;
+        sp.rows = RowKeys{x->db, x->row_bytes, view_of(x).P};
         rc = sort_segments(sp, sort_scratch, s);
+    }
+    if (rc == kSortNeedsLow) {
+        // a run of equal high words too long for the fix-up: compute the low
+        // words and sort by every key byte (the high words are rewritten
+        // with the same values; the sorted low words are dropped)
+        uint64_t* lo_buf = nullptr;
+        rc = dev_alloc_async((void**)&lo_buf, sizeof(uint64_t) * 2 * total, s);
+        if (rc == HC_OK) {
+            BuildKeysArgs kb = ka;
+            kb.lo = lo_buf;
+            rc = status_of(launch_build_keys(kb, s));
+            if (rc == HC_OK) {
+                sp.lo = lo_buf;
+                sp.out_lo = lo_buf + total;
+                sp.allow_sync = false;
+                rc = sort_segments(sp, sort_scratch, s);
+            }
+            const int lrc = status_of(cudaFreeAsync(lo_buf, s));
+            if (rc == HC_OK) rc = lrc;
+        }
     }
     const int frc = status_of(cudaFreeAsync(scratch, s));
     return rc ? rc : frc;
@@ -383,8 +409,9 @@ HC_API int hc_index_copy_lists(const hc_index* idx, uint64_t* keys_hi_dev, uint6
     int rc = status_of(cudaMemcpyAsync(keys_hi_dev, idx->keys_hi, 8 * total,
                                        cudaMemcpyDeviceToDevice, s));
     if (!rc)
-        rc = status_of(cudaMemcpyAsync(keys_lo_dev, idx->keys_lo, 8 * total,
-                                       cudaMemcpyDeviceToDevice, s));
+        rc = status_of(idx->keys_lo ? cudaMemcpyAsync(keys_lo_dev, idx->keys_lo, 8 * total,
+                                                      cudaMemcpyDeviceToDevice, s)
+                                    : launch_entry_lo(view_of(idx), keys_lo_dev, s));
     if (!rc)
         rc = status_of(cudaMemcpyAsync(ids_dev, idx->ids, 4 * total, cudaMemcpyDeviceToDevice, s));
     return rc;

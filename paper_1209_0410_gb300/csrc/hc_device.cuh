@@ -258,6 +258,15 @@ __device__ __forceinline__ void curve_key(const void* row, const Projection& P, 
     hilbert_key_m(P.m, X, hi, lo);
 }
 
+// Low key word of one row on curve c (the index keeps high words only when
+// they carry 64 key bits; ties of the high words are rare and decided here).
+__device__ __forceinline__ uint64_t row_key_lo(const void* db, uint32_t row_bytes,
+                                               const Projection& P, uint32_t row, uint32_t c) {
+    uint64_t h, l;
+    curve_key(static_cast<const uint8_t*>(db) + (size_t)row * row_bytes, P, c, h, l);
+    return l;
+}
+
 // Partition of row r when n rows are split into l contiguous ranges
 // [floor(j*n/l), floor((j+1)*n/l)): the largest j whose range starts at or
 // before r, i.e. floor(((r+1)*l - 1) / n).

@@ -41,6 +41,13 @@ cudaError_t launch_vector_keys(const void* x, uint64_t count, uint32_t row_bytes
 // ------------------------------------------------------------ K2: sort
 // Stable LSD radix sort of 128-bit keys by segment.  The sources stay
 // untouched; the sorted keys and the carried ids land in out_*.
+// Where the key of a database row comes from: the rows and their projection.
+struct RowKeys {
+    const void* db = nullptr;
+    uint32_t row_bytes = 0;
+    Projection P{};
+};
+
 struct SortProblem {
     const uint64_t* hi;        // device, total records
     const uint64_t* lo;
@@ -57,10 +64,18 @@ struct SortProblem {
     int hi_skip = 0;
     const uint64_t* id_base_dev = nullptr;  // device, nseg: ids[i] = id_base[s] + i - seg start
                                             // (then `ids` is not read); null = gather ids
+    // lo == nullptr (high-word-first path with affine ids only): the low word
+    // of record i of segment s is recomputed from row id_base[s] + i - seg
+    // start on curve s % rows.P.curves, when a tie of the high words needs
+    // it; out_lo is not written.  A run of equal high-word prefixes too long
+    // for the fix-up then returns kSortNeedsLow (the caller supplies lo and
+    // sorts again).
+    RowKeys rows{};
     uint64_t* out_hi;          // device, total records (distinct from sources)
     uint64_t* out_lo;
     uint32_t* out_ids;
 };
+constexpr int kSortNeedsLow = 2;
 // Scratch bytes the sort needs for this problem (queried before allocating).
 size_t sort_scratch_bytes(const SortProblem& p);
 // Enqueues the whole sort on s using the given scratch (>= sort_scratch_bytes).
@@ -81,13 +96,15 @@ struct IndexView {
     uint32_t lists;            // partitions * curves
     const uint64_t* list_off;  // device, lists+1
     const uint64_t* keys_hi;
-    const uint64_t* keys_lo;
+    const uint64_t* keys_lo;   // null: low words recomputed from the rows (16-coordinate keys)
     const uint32_t* ids;
 };
 
 // p_query (device, nq entries, nullable) gives each query its own depth.
 // pos_in (device, nq x lists, nullable): lower_bound positions computed
 // earlier (hc_query_positions), so the kernel skips its own search.
+// Low key words of every entry (list_off order) of an index without keys_lo.
+cudaError_t launch_entry_lo(const IndexView& ix, uint64_t* out, cudaStream_t s);
 cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids, void* out_dist, cudaStream_t s,
                          const uint32_t* p_query = nullptr, const int64_t* pos_in = nullptr);

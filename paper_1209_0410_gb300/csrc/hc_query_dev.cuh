@@ -150,16 +150,22 @@ __device__ __forceinline__ uint64_t chunk_candidates(const uint8_t* __restrict__
     return out[0];
 }
 
-// first i in [0, n) with key[i] >= (kh, kl), else n
-__device__ __forceinline__ uint32_t lower_bound_key(const uint64_t* __restrict__ hi,
-                                                    const uint64_t* __restrict__ lo, uint32_t n,
-                                                    uint64_t kh, uint64_t kl) {
+// Low key word of entry g (global entry index) of list L.
+__device__ __forceinline__ uint64_t entry_key_lo(const IndexView& ix, uint32_t L, uint64_t g) {
+    if (ix.keys_lo) return __ldg(ix.keys_lo + g);
+    return row_key_lo(ix.db, ix.row_bytes, ix.P, __ldg(ix.ids + g), L % ix.P.curves);
+}
+
+// first i in [0, n) of list L (entries off ..) with key[i] >= (kh, kl), else n;
+// the low word is consulted only when the high words tie
+__device__ __forceinline__ uint32_t lower_bound_key(const IndexView& ix, uint32_t L, uint64_t off,
+                                                    uint32_t n, uint64_t kh, uint64_t kl) {
     uint32_t first = 0, count = n;
     while (count > 0) {
         const uint32_t step = count >> 1, mid = first + step;
-        const uint64_t h = __ldg(hi + mid);
+        const uint64_t h = __ldg(ix.keys_hi + off + mid);
         bool less = h < kh;
-        if (h == kh) less = __ldg(lo + mid) < kl;
+        if (h == kh) less = entry_key_lo(ix, L, off + mid) < kl;
         if (less) {
             first = mid + 1;
             count -= step + 1;
@@ -188,7 +194,7 @@ __device__ __forceinline__ void query_positions(const IndexView& ix, const uint8
         if (t < mine) {
             const uint64_t off = ix.list_off[L];
             const uint32_t n = (uint32_t)(ix.list_off[L + 1] - off);
-            pos_w[L] = lower_bound_key(ix.keys_hi + off, ix.keys_lo + off, n, kh, kl);
+            pos_w[L] = lower_bound_key(ix, L, off, n, kh, kl);
         }
     }
     __syncwarp();

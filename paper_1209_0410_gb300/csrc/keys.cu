@@ -2,7 +2,8 @@
 // and of standalone vectors.  One thread per row computes the keys of every
 // curve; the Hilbert map itself is ALU work (about 800 integer operations
 // per 16-coordinate key), the row read and the 20 bytes written per key are
-// coalesced across the warp.
+// coalesced across the warp (the low words are written only when the index
+// keeps them).
 #include "hc_internal.h"
 
 namespace hc {
@@ -26,7 +27,7 @@ __global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
                 for (int t = 0; t < 4; ++t) {
                     const uint64_t g = a.list_off[part * a.P.curves + c + t] + local;
                     a.hi[g] = hi[t];
-                    a.lo[g] = lo[t];
+                    if (a.lo) a.lo[g] = lo[t];
                     if (a.ids) a.ids[g] = (uint32_t)r;
                 }
             }
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
             curve_key(row, a.P, c, hi, lo);
             const uint64_t g = a.list_off[part * a.P.curves + c] + local;
             a.hi[g] = hi;
-            a.lo[g] = lo;
+            if (a.lo) a.lo[g] = lo;
             if (a.ids) a.ids[g] = (uint32_t)r;
         }
     }
@@ -55,6 +56,17 @@ __global__ void __launch_bounds__(256) vector_keys_kernel(const void* x, uint64_
         hi[t] = h;
         lo[t] = l;
     }
+}
+
+// low key words of every entry of an index that keeps high words only
+// (grid y = list)
+__global__ void __launch_bounds__(256) entry_lo_kernel(IndexView ix, uint64_t* __restrict__ out) {
+    const uint32_t L = blockIdx.y;
+    const uint64_t off = ix.list_off[L], n = ix.list_off[L + 1] - off;
+    const uint32_t c = L % ix.P.curves;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        out[off + i] = row_key_lo(ix.db, ix.row_bytes, ix.P, __ldg(ix.ids + off + i), c);
 }
 
 static unsigned grid_for(uint64_t work, unsigned threads) {
@@ -78,6 +90,13 @@ cudaError_t launch_vector_keys(const void* x, uint64_t count, uint32_t row_bytes
     if (count == 0) return cudaSuccess;
     vector_keys_kernel<<<grid_for(count * P.curves, 256), 256, 0, s>>>(x, count, row_bytes, P, hi,
                                                                        lo);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_entry_lo(const IndexView& ix, uint64_t* out, cudaStream_t s) {
+    if (ix.lists == 0) return cudaSuccess;
+    entry_lo_kernel<<<dim3(64, ix.lists), 256, 0, s>>>(ix, out);
     count_launches(1);
     return cudaGetLastError();
 }

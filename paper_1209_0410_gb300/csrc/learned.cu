@@ -383,12 +383,14 @@ __device__ void query_features(const IndexView& ix, const uint8_t* qrow, uint4 q
         if (lane == 0) {
             float f0 = kFeatNone, f1 = kFeatNone, f2 = kFeatNone, f3 = kFeatNone;
             if (pos > 0) {
-                const uint64_t ph = ix.keys_hi[off + pos - 1], pl = ix.keys_lo[off + pos - 1];
+                const uint64_t ph = ix.keys_hi[off + pos - 1];
+                const uint64_t pl = entry_key_lo(ix, c, off + pos - 1);
                 const uint64_t gl = kl - pl, gh = kh - ph - (kl < pl ? 1u : 0u);
                 f0 = octave128(gh, gl);
             }
             if (pos < n) {
-                const uint64_t nh = ix.keys_hi[off + pos], nl = ix.keys_lo[off + pos];
+                const uint64_t nh = ix.keys_hi[off + pos];
+                const uint64_t nl = entry_key_lo(ix, c, off + pos);
                 const uint64_t gl = nl - kl, gh = nh - kh - (nl < kl ? 1u : 0u);
                 f1 = octave128(gh, gl);
             }
@@ -415,7 +417,7 @@ __device__ __forceinline__ void warp_keys_positions(const IndexView& ix, const u
     if ((uint32_t)lane < curves) {
         const uint64_t off = ix.list_off[lane];
         const uint32_t n = (uint32_t)(ix.list_off[lane + 1] - off);
-        pos_w[lane] = lower_bound_key(ix.keys_hi + off, ix.keys_lo + off, n, khi, klo);
+        pos_w[lane] = lower_bound_key(ix, (uint32_t)lane, off, n, khi, klo);
     }
     __syncwarp();
 }

@@ -39,6 +39,7 @@ struct MultiTask {
 
 constexpr int kMaxWarps = 16;
 constexpr uint32_t kMaxLists = 256;
+constexpr size_t kRingBytes = 64 * 128;   // two 32-row steps of rows up to 128 bytes
 
 // Instantiations inside the persistent kernel: row classes uint8 with 4, 8 or
 // 16 lanes per row (wider uint8 rows take 16 lanes and loop), float32 with 16
@@ -58,14 +59,25 @@ uint32_t variant_of(hc_dtype t, uint32_t row_bytes, uint32_t k) {
 // merge; templated on the job's variant.
 // group_buf: 4 x 32 slots per warp of the query's group (warp `sub` owns
 // group_buf + sub * 128).
+// ring: the warp's two-step row ring (64 x 128 bytes) when the plan has
+// rows of at most 128 bytes, else null.
 template <bool F32, int LPR, int KR>
 __device__ void multi_query(const MultiJob& J, uint32_t qi, bool active, uint32_t sub,
-                            uint32_t* pos_w, uint64_t* group_buf, int lane) {
+                            uint32_t* pos_w, uint64_t* group_buf, uint8_t* ring, int lane) {
     WarpTopK<KR> top;
     top.init();
     if (active) {
         const uint8_t* qrow = J.q + (size_t)qi * J.ix.row_bytes;
-        search_lists<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w, top, lane);
+        if constexpr (LPR <= 8) {
+            if (ring && J.ix.row_bytes <= 128) {
+                search_lists_staged<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w, ring,
+                                                  top, lane);
+            } else {
+                search_lists<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w, top, lane);
+            }
+        } else {
+            search_lists<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w, top, lane);
+        }
     }
     // every warp publishes its list; the group leader folds the others in
     uint64_t* mine = group_buf + (size_t)sub * 4 * 32;
@@ -87,20 +99,22 @@ __device__ void multi_query(const MultiJob& J, uint32_t qi, bool active, uint32_
 template <int V>
 __device__ __forceinline__ void run_variant(const MultiJob& J, uint32_t qi, bool active,
                                             uint32_t sub, uint32_t* pos_w, uint64_t* mb,
-                                            int lane) {
+                                            uint8_t* ring, int lane) {
     constexpr int CLS = V / 2;
     constexpr bool F32 = CLS >= 3;
     constexpr int LPR = CLS == 0 ? 4 : (CLS == 1 ? 8 : (CLS == 2 ? 16 : (CLS == 3 ? 16 : 32)));
     constexpr int KR = (V & 1) ? 4 : 1;
-    multi_query<F32, LPR, KR>(J, qi, active, sub, pos_w, mb, lane);
+    multi_query<F32, LPR, KR>(J, qi, active, sub, pos_w, mb, ring, lane);
 }
 
 __global__ void multi_kernel(const MultiJob* __restrict__ jobs, const MultiTask* __restrict__ tasks,
-                             uint32_t ntasks, uint32_t tile, uint32_t* __restrict__ counter) {
+                             uint32_t ntasks, uint32_t tile, uint32_t* __restrict__ counter,
+                             bool staged) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t nwarps = blockDim.x >> 5;
     uint64_t* merge = reinterpret_cast<uint64_t*>(smem_raw);             // nwarps x 4 x 32
     uint32_t* pos = reinterpret_cast<uint32_t*>(merge + nwarps * 4 * 32); // nwarps x kMaxLists
+    uint8_t* rings = reinterpret_cast<uint8_t*>(pos + nwarps * kMaxLists); // nwarps x kRingBytes
     __shared__ uint32_t s_task;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = threadIdx.x >> 5;
@@ -120,9 +134,10 @@ __global__ void multi_kernel(const MultiJob* __restrict__ jobs, const MultiTask*
             const bool active = group < per_pass && qo < T.cnt;
             const uint32_t qi = T.q0 + qo;
             uint32_t* pw = pos + (size_t)warp * kMaxLists;
+            uint8_t* ring = staged ? rings + (size_t)warp * kRingBytes : nullptr;
             switch (J.variant) {
 #define HC_V(n) \
-    case n: run_variant<n>(J, qi, active, sub, pw, mb, lane); break;
+    case n: run_variant<n>(J, qi, active, sub, pw, mb, ring, lane); break;
                 HC_V(0) HC_V(1) HC_V(2) HC_V(3) HC_V(4) HC_V(5) HC_V(6) HC_V(7) HC_V(8)
                 HC_V(9)
 #undef HC_V
@@ -135,8 +150,9 @@ __global__ void multi_kernel(const MultiJob* __restrict__ jobs, const MultiTask*
 
 __global__ void reset_counter_kernel(uint32_t* c) { *c = 0; }
 
-size_t multi_smem(uint32_t nwarps) {
-    return (size_t)nwarps * 4 * 32 * sizeof(uint64_t) + (size_t)nwarps * kMaxLists * sizeof(uint32_t);
+size_t multi_smem(uint32_t nwarps, bool staged) {
+    return (size_t)nwarps * 4 * 32 * sizeof(uint64_t) +
+           (size_t)nwarps * kMaxLists * sizeof(uint32_t) + (staged ? nwarps * kRingBytes : 0);
 }
 
 }  // namespace
@@ -149,6 +165,7 @@ struct hc_multi_plan {
     uint32_t* counter = nullptr;
     unsigned grid = 0;
     size_t smem = 0;
+    bool staged = false;   // some job has rows of at most 128 bytes and <= 8 lanes per row
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -168,7 +185,7 @@ bool on_device(const void* p) {
 int enqueue(hc_multi_plan* P, cudaStream_t s) {
     reset_counter_kernel<<<1, 1, 0, s>>>(P->counter);
     multi_kernel<<<P->grid, P->cfg.warps_per_block * 32, P->smem, s>>>(
-        P->jobs_dev, P->tasks_dev, P->ntasks, P->cfg.tile, P->counter);
+        P->jobs_dev, P->tasks_dev, P->ntasks, P->cfg.tile, P->counter, P->staged);
     count_launches(2);
     return cudaGetLastError() == cudaSuccess ? HC_OK : HC_ERR_CUDA;
 }
@@ -268,7 +285,8 @@ HC_API int hc_multi_plan_create(const hc_multi_job* jobs, uint32_t njobs,
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    P->smem = multi_smem(cfg.warps_per_block);
+    for (const MultiJob& j : hj) P->staged |= j.variant / 2 <= 1;   // uint8 rows <= 128 bytes
+    P->smem = multi_smem(cfg.warps_per_block, P->staged);
     if (cudaFuncSetAttribute(multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)P->smem) != cudaSuccess) {
         free_plan(P);

@@ -320,9 +320,11 @@ __global__ void __launch_bounds__(256) gather_final_kernel(
 // redoes the sort with every digit.  The low words and ids are gathered here.
 constexpr uint32_t kMaxRun = 32;
 
+// lo == nullptr: low words are recomputed from the rows (affine ids) when
+// two records of a run have equal high words, and out_lo is not written.
 __global__ void __launch_bounds__(256) fixup_final_kernel(
     const uint64_t* __restrict__ w, int run_shift, const uint32_t* __restrict__ pos,
-    const uint64_t* __restrict__ lo, FinalIds fid, uint64_t* __restrict__ out_hi,
+    const uint64_t* __restrict__ lo, RowKeys rows, FinalIds fid, uint64_t* __restrict__ out_hi,
     uint64_t* __restrict__ out_lo, uint32_t* __restrict__ out_ids, uint32_t nseg,
     const SegInfo* __restrict__ segs, uint32_t* __restrict__ long_run) {
     SegInfo si;
@@ -331,12 +333,14 @@ __global__ void __launch_bounds__(256) fixup_final_kernel(
     tile_of(nseg, segs, si, seg, lt, start, count);
     const uint64_t id_base = fid.id_base ? __ldg(fid.id_base + seg) - si.start : 0;
     const uint64_t seg_end = si.start + si.len;
+    const uint32_t curve = lo ? 0u : seg % rows.P.curves;
     for (uint32_t t = threadIdx.x; t < count; t += blockDim.x) {
         const uint64_t i = start + t;
         const uint64_t wi = __ldg(w + i);
         const uint64_t key = wi >> run_shift;
         const uint32_t pi = __ldg(pos + i);
-        const uint64_t li = __ldg(lo + pi);
+        uint64_t li = lo ? __ldg(lo + pi) : 0;
+        bool li_ok = lo != nullptr;
         const uint32_t idi = fid.id_base ? (uint32_t)(id_base + pi) : __ldg(fid.ids + pi);
         const bool prev_eq = i > si.start && (__ldg(w + i - 1) >> run_shift) == key;
         const bool next_eq = i + 1 < seg_end && (__ldg(w + i + 1) >> run_shift) == key;
@@ -356,7 +360,14 @@ __global__ void __launch_bounds__(256) fixup_final_kernel(
                     const uint32_t pj = __ldg(pos + j);
                     bool before = wj < wi;
                     if (wj == wi) {
-                        const uint64_t lj = __ldg(lo + pj);
+                        if (!li_ok) {
+                            li = row_key_lo(rows.db, rows.row_bytes, rows.P, idi, curve);
+                            li_ok = true;
+                        }
+                        const uint64_t lj =
+                            lo ? __ldg(lo + pj)
+                               : row_key_lo(rows.db, rows.row_bytes, rows.P,
+                                            (uint32_t)(id_base + pj), curve);
                         before = lj < li || (lj == li && pj < pi);
                     }
                     rank += before ? 1u : 0u;
@@ -365,7 +376,7 @@ __global__ void __launch_bounds__(256) fixup_final_kernel(
             }
         }
         out_hi[dst] = wi;
-        out_lo[dst] = li;
+        if (out_lo) out_lo[dst] = li;
         out_ids[dst] = idi;
     }
 }
@@ -501,9 +512,9 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
         }
         if (cw != wtmp) return HC_ERR_STATE;
         if (cudaMemsetAsync(flag, 0, sizeof(uint32_t), s) != cudaSuccess) return HC_ERR_CUDA;
-        fixup_final_kernel<<<L.ntiles, 256, 0, s>>>(wtmp, 8 * skip, cp, p.lo,
-                                                     FinalIds{p.ids, p.id_base_dev}, p.out_hi,
-                                                     p.out_lo, p.out_ids, L.nseg, segs, flag);
+        fixup_final_kernel<<<L.ntiles, 256, 0, s>>>(
+            wtmp, 8 * skip, cp, p.lo, p.rows, FinalIds{p.ids, p.id_base_dev}, p.out_hi,
+            p.lo ? p.out_lo : nullptr, p.out_ids, L.nseg, segs, flag);
         count_launches(1);
         if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
         uint32_t long_run = 1;
@@ -514,7 +525,9 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
         if (!long_run) return HC_OK;
         // a run of equal high words longer than the fix-up handles: sort
         // again with every digit (the sources are untouched)
+        if (!p.lo) return kSortNeedsLow;
     }
+    if (!p.lo) return kSortNeedsLow;   // every digit needs the low words
     // word buffers written in sequence: each lo pass, the hi gather, each hi
     // pass; alternate so that the last write lands in out_hi.
     const int writes = lo_passes + 1 + hi_passes;

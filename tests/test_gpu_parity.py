@@ -270,6 +270,33 @@ def test_duplicate_rows_rank_lower_id_first(hc):
         assert g[i].tolist() == [i, i + 1500, i + 3000, i + 4500]
 
 
+@pytest.mark.parametrize("parts", [1, 3])
+def test_build_long_runs_of_equal_keys(hc, parts):
+    """More than 32 rows with one key: the high-word fix-up cannot order the
+    run, so the build computes the low words and sorts by every key byte;
+    the lists (low words recomputed from the rows) and queries (which tie on
+    the high word and read low words from rows) still match the oracle."""
+    rng = np.random.default_rng(17)
+    base = rng.integers(0, 256, size=(60, 128), dtype=np.uint8)
+    db = np.concatenate([np.repeat(base, 40, axis=0),
+                         rng.integers(0, 256, size=(3001, 128), dtype=np.uint8)])
+    db = db[rng.permutation(len(db))]
+    idx = hc.hc_build(dev(db), partitions=parts)
+    hi, lo, ids, off = hc.hc_index_copy_lists(idx)
+    sync()
+    oidx = O.build(db, curves=8, m=16, ell=parts)
+    assert np.array_equal(u64(hi), oidx.keys_hi)
+    assert np.array_equal(u64(lo), oidx.keys_lo)
+    assert np.array_equal(ids.cpu().numpy().astype(np.int64), oidx.ids.astype(np.int64))
+    q = np.concatenate([base[:20], db[:30]])
+    rids, rdist = O.search(oidx, db, q, 10, 24)
+    gids, gdist = hc.hc_query(idx, dev(q), 10, 24)
+    sync()
+    assert np.array_equal(gids.cpu().numpy(), rids)
+    assert np.array_equal(gdist.cpu().numpy(), O.int32_dist(rdist))
+    idx.free()
+
+
 @pytest.mark.parametrize("nq", [0, 1, 7, 9, 1000])
 def test_query_batch_sizes(hc, nq):
     n = 6000
