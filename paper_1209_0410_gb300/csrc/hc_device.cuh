@@ -113,6 +113,12 @@ __device__ __forceinline__ void transpose4x4_bytes(uint32_t a0, uint32_t a1, uin
 // byte-parallel logic (per-byte masks from a multiply by 0xFF, which runs on
 // the FMA pipe and spares the integer ALU pipe).  c[k] holds key k's 16
 // coordinate bytes (coordinate i = byte i % 4 of word i / 4).
+// HI_ONLY: only the high words (bit planes 7..4) are wanted.  Level q changes
+// only bits below q and decides on bit q, so planes 7..4 are final after the
+// levels 7, 6 and 5; the Gray code and the correction of a plane depend on
+// that plane and the planes above it.  Levels 4..1 are skipped and lo is
+// left unset.
+template <bool HI_ONLY = false>
 __device__ __forceinline__ void hilbert_keys4(const uint4 (&c)[4], uint64_t (&hi)[4],
                                               uint64_t (&lo)[4]) {
     constexpr uint32_t ONES = 0x01010101u;
@@ -131,7 +137,7 @@ __device__ __forceinline__ void hilbert_keys4(const uint4 (&c)[4], uint64_t (&hi
         }
     }
 #pragma unroll
-    for (int q = 7; q >= 1; --q) {
+    for (int q = 7; q >= (HI_ONLY ? 5 : 1); --q) {
         const uint32_t low = ((1u << q) - 1u) * ONES;
         X[0] ^= low & (((X[0] >> q) & ONES) * 0xFFu);
 #pragma unroll
@@ -163,8 +169,9 @@ __device__ __forceinline__ void hilbert_keys4(const uint4 (&c)[4], uint64_t (&hi
         const uint32_t Bl = (uint32_t)B, Bh = (uint32_t)(B >> 32);
         hi[k] = ((uint64_t)__brev(__byte_perm(Ah, Bh, 0x6273)) << 32) |
                 __brev(__byte_perm(Ah, Bh, 0x4051));
-        lo[k] = ((uint64_t)__brev(__byte_perm(Al, Bl, 0x6273)) << 32) |
-                __brev(__byte_perm(Al, Bl, 0x4051));
+        if (!HI_ONLY)
+            lo[k] = ((uint64_t)__brev(__byte_perm(Al, Bl, 0x6273)) << 32) |
+                    __brev(__byte_perm(Al, Bl, 0x4051));
     }
 }
 

@@ -22,7 +22,10 @@ __global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
 #pragma unroll
                 for (int t = 0; t < 4; ++t) cb[t] = curve_bytes16(row, a.P.dtype, c + t);
                 uint64_t hi[4], lo[4];
-                hilbert_keys4(cb, hi, lo);
+                if (a.lo)
+                    hilbert_keys4<false>(cb, hi, lo);
+                else
+                    hilbert_keys4<true>(cb, hi, lo);
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const uint64_t g = a.list_off[part * a.P.curves + c + t] + local;
