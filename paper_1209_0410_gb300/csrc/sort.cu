@@ -180,11 +180,13 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
 // the warp's running digit counts); the digit-major scan of the 16 x 256
 // counts then gives every record its place in the digit-sorted tile, stable
 // in record order.  Records past the tile's end carry digit 255 and sort last.
+// id_base (final pass of an affine-id sort, else null): the carried
+// positions leave as ids, id = id_base[seg] + position - segment start.
 __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
     const uint64_t* __restrict__ wsrc, const uint32_t* __restrict__ psrc,
     uint64_t* __restrict__ wdst, uint32_t* __restrict__ pdst, int shift, uint32_t nseg,
     const SegInfo* __restrict__ segs, const uint32_t* __restrict__ counts,
-    const uint32_t* __restrict__ totals) {
+    const uint32_t* __restrict__ totals, const uint64_t* __restrict__ id_base) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
 
@@ -257,11 +259,12 @@ __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
         sm.p[padp(slot)] = p[r];
     }
     __syncthreads();
+    const uint32_t idoff = id_base ? (uint32_t)(__ldg(id_base + seg) - si.start) : 0u;
     for (uint32_t i = t; i < count; i += kSThreads) {
         const uint64_t v = sm.w[padw(i)];
         const uint64_t g = sm.gbase[(uint32_t)(v >> shift) & 0xFFu] + i;
         wdst[g] = v;
-        pdst[g] = sm.p[padp(i)];
+        pdst[g] = sm.p[padp(i)] + idoff;
     }
 }
 
@@ -381,6 +384,75 @@ __global__ void __launch_bounds__(256) fixup_final_kernel(
     }
 }
 
+// In-place fix-up after a sort whose last pass wrote the final high words
+// and ids (affine ids, low words recomputed from rows).  Runs of equal
+// prefixes hi >> run_shift (ordered by id, i.e. by position) must end
+// ordered by (hi, low word, id).  A warp walks 32 records at a time; each run
+// that starts among them (at most kMaxRun = 32 records; a longer one sets
+// *long_run) is then sorted by the whole warp, one record per lane: lanes
+// whose high words tie compute their low words, every lane counts the run's
+// records below its own, and all lanes write after all have read.  Other
+// warps only read prefixes, which a permutation inside a run leaves
+// unchanged, so the in-place writes race with nothing.
+__global__ void __launch_bounds__(256) fixup_runs_kernel(uint64_t* hi, uint32_t* ids, int run_shift,
+                                                         RowKeys rows, uint32_t nseg,
+                                                         const SegInfo* __restrict__ segs,
+                                                         uint32_t* __restrict__ long_run) {
+    static_assert(kMaxRun == 32, "one run record per lane");
+    SegInfo si;
+    uint32_t seg, lt, count;
+    uint64_t start;
+    tile_of(nseg, segs, si, seg, lt, start, count);
+    const uint64_t seg_end = si.start + si.len;
+    const uint32_t curve = seg % rows.P.curves;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t base = warp * 32; base < count; base += nwarps * 32) {
+        const uint64_t i = start + base + lane;
+        bool run_start = false;
+        if (base + lane < count && i + 1 < seg_end) {
+            const uint64_t key = hi[i] >> run_shift;
+            run_start = (hi[i + 1] >> run_shift) == key &&
+                        !(i > si.start && (hi[i - 1] >> run_shift) == key);
+        }
+        uint32_t starts = __ballot_sync(0xffffffffu, run_start);
+        while (starts) {
+            const int src = __ffs(starts) - 1;
+            starts &= starts - 1;
+            const uint64_t rs = start + base + src;
+            const uint64_t key = hi[rs] >> run_shift;
+            const uint64_t e = rs + lane;
+            const bool in = e < seg_end && (hi[e] >> run_shift) == key;
+            const uint32_t inmask = __ballot_sync(0xffffffffu, in);
+            const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
+            if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == key) {
+                if (lane == 0) atomicOr(long_run, 1u);
+                continue;
+            }
+            const bool mine = (uint32_t)lane < len;
+            const uint64_t h = mine ? hi[e] : ~0ull;
+            const uint32_t d = mine ? ids[e] : 0xFFFFFFFFu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, h);
+            const uint64_t l = (mine && __popc(peers) > 1)
+                                   ? row_key_lo(rows.db, rows.row_bytes, rows.P, d, curve)
+                                   : 0;
+            uint32_t rank = 0;
+            for (uint32_t u = 0; u < len; ++u) {
+                const uint64_t hu = __shfl_sync(0xffffffffu, h, (int)u);
+                const uint64_t lu = __shfl_sync(0xffffffffu, l, (int)u);
+                const uint32_t du = __shfl_sync(0xffffffffu, d, (int)u);
+                rank += (hu < h || (hu == h && (lu < l || (lu == l && du < d)))) ? 1u : 0u;
+            }
+            __syncwarp();
+            if (mine) {
+                hi[rs + rank] = h;
+                ids[rs + rank] = d;
+            }
+            __syncwarp();
+        }
+    }
+}
+
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 uint32_t* pbuf_of(uint32_t* a, uint32_t* b, int which) { return which ? b : a; }
@@ -491,30 +563,42 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
         // hi_skip digits when more remain), then order runs of equal prefixes
         const int skip = (p.hi_skip > 0 && hi_passes > p.hi_skip) ? p.hi_skip : 0;
         const int npass = hi_passes - skip;
+        // affine ids without low words: the last pass writes the final high
+        // words and ids, and only runs are fixed up in place
+        const bool in_place = p.lo == nullptr && p.id_base_dev != nullptr;
         uint64_t* wb[2] = {wtmp, p.out_hi};
-        int wn = (npass % 2 == 1) ? 0 : 1;   // the last pass writes wtmp
+        // the last pass writes wtmp (or out_hi when in place)
+        int wn = ((npass % 2 == 1) != in_place) ? 0 : 1;
         int pn = 0;
         const uint64_t* cw = p.hi;
         const uint32_t* cp = nullptr;
         for (int t = 8 + skip; t < 8 + hi_passes; ++t) {
             const int shift = (t & 7) * 8;
+            const bool last = t + 1 == 8 + hi_passes;
+            uint32_t* pd = (last && in_place) ? p.out_ids : pbuf_of(pa, pb, pn);
             hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cw, shift, L.nseg, segs, counts);
             scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
-            scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(cw, cp, wb[wn], pbuf_of(pa, pb, pn),
-                                                                 shift, L.nseg, segs, counts,
-                                                                 totals);
+            scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(
+                cw, cp, wb[wn], pd, shift, L.nseg, segs, counts, totals,
+                (last && in_place) ? p.id_base_dev : nullptr);
             count_launches(3);
             if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
             cw = wb[wn];
-            cp = pbuf_of(pa, pb, pn);
+            cp = pd;
             wn ^= 1;
             pn ^= 1;
         }
-        if (cw != wtmp) return HC_ERR_STATE;
         if (cudaMemsetAsync(flag, 0, sizeof(uint32_t), s) != cudaSuccess) return HC_ERR_CUDA;
-        fixup_final_kernel<<<L.ntiles, 256, 0, s>>>(
-            wtmp, 8 * skip, cp, p.lo, p.rows, FinalIds{p.ids, p.id_base_dev}, p.out_hi,
-            p.lo ? p.out_lo : nullptr, p.out_ids, L.nseg, segs, flag);
+        if (in_place) {
+            if (cw != p.out_hi) return HC_ERR_STATE;
+            fixup_runs_kernel<<<L.ntiles, 256, 0, s>>>(p.out_hi, p.out_ids, 8 * skip, p.rows,
+                                                       L.nseg, segs, flag);
+        } else {
+            if (cw != wtmp) return HC_ERR_STATE;
+            fixup_final_kernel<<<L.ntiles, 256, 0, s>>>(
+                wtmp, 8 * skip, cp, p.lo, p.rows, FinalIds{p.ids, p.id_base_dev}, p.out_hi,
+                p.lo ? p.out_lo : nullptr, p.out_ids, L.nseg, segs, flag);
+        }
         count_launches(1);
         if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
         uint32_t long_run = 1;
@@ -546,7 +630,8 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             uint64_t* wd = wbuf[wnext];
             uint32_t* pd = pbuf[pnext];
             scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(cur_w, cur_p, wd, pd, shift,
-                                                                L.nseg, segs, counts, totals);
+                                                                L.nseg, segs, counts, totals,
+                                                                nullptr);
             count_launches(3);
             if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
             cur_w = wd;

@@ -270,15 +270,16 @@ def test_duplicate_rows_rank_lower_id_first(hc):
         assert g[i].tolist() == [i, i + 1500, i + 3000, i + 4500]
 
 
-@pytest.mark.parametrize("parts", [1, 3])
-def test_build_long_runs_of_equal_keys(hc, parts):
-    """More than 32 rows with one key: the high-word fix-up cannot order the
-    run, so the build computes the low words and sorts by every key byte;
-    the lists (low words recomputed from the rows) and queries (which tie on
-    the high word and read low words from rows) still match the oracle."""
+@pytest.mark.parametrize("parts,copies", [(1, 40), (3, 40), (1, 32), (1, 33), (2, 31)])
+def test_build_long_runs_of_equal_keys(hc, parts, copies):
+    """Rows repeated `copies` times: runs of equal keys up to 32 are ordered
+    by the in-place fix-up (ties of the high word read low words from the
+    rows); longer runs make the build compute the low words and sort by every
+    key byte.  The lists (low words recomputed from the rows) and queries
+    (which tie on the high word) match the oracle either way."""
     rng = np.random.default_rng(17)
     base = rng.integers(0, 256, size=(60, 128), dtype=np.uint8)
-    db = np.concatenate([np.repeat(base, 40, axis=0),
+    db = np.concatenate([np.repeat(base, copies, axis=0),
                          rng.integers(0, 256, size=(3001, 128), dtype=np.uint8)])
     db = db[rng.permutation(len(db))]
     idx = hc.hc_build(dev(db), partitions=parts)
