@@ -224,9 +224,11 @@ __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
     __syncthreads();
 
     // digit-major exclusive scan of hist[warp][digit]: thread t owns digit
-    // t / 2, warps 8 (t % 2) .. 8 (t % 2) + 7
+    // t / tpd, warps 8 (t % tpd) .. 8 (t % tpd) + 7 (tpd = threads per digit)
     {
-        const uint32_t d = (uint32_t)t >> 1, w0 = ((uint32_t)t & 1u) * 8;
+        constexpr uint32_t tpd = kSThreads / 256;
+        static_assert(kSWarps == 8 * tpd, "eight warps per thread slot");
+        const uint32_t d = (uint32_t)t / tpd, w0 = ((uint32_t)t % tpd) * 8;
         uint32_t v[8], sum = 0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
