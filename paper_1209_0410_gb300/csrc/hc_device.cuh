@@ -265,12 +265,21 @@ __device__ __forceinline__ void curve_key(const void* row, const Projection& P, 
     hilbert_key_m(P.m, X, hi, lo);
 }
 
+// curve_key out of line, for code that computes a few keys per query (one
+// copy per translation unit instead of one per kernel instantiation)
+static __device__ __noinline__ void curve_key_call(const void* row, const Projection& P, uint32_t c,
+                                            uint64_t& hi, uint64_t& lo) {
+    curve_key(row, P, c, hi, lo);
+}
+
 // Low key word of one row on curve c (the index keeps high words only when
 // they carry 64 key bits; ties of the high words are rare and decided here).
-__device__ __forceinline__ uint64_t row_key_lo(const void* db, uint32_t row_bytes,
-                                               const Projection& P, uint32_t row, uint32_t c) {
+// (out of line: it is on rare paths, and one copy per translation unit keeps
+// the many query-kernel instantiations small)
+static __device__ __noinline__ uint64_t row_key_lo(const void* db, uint32_t row_bytes,
+                                            const Projection& P, uint32_t row, uint32_t c) {
     uint64_t h, l;
-    curve_key(static_cast<const uint8_t*>(db) + (size_t)row * row_bytes, P, c, h, l);
+    curve_key_call(static_cast<const uint8_t*>(db) + (size_t)row * row_bytes, P, c, h, l);
     return l;
 }
 

@@ -183,7 +183,7 @@ __device__ __forceinline__ void query_positions(const IndexView& ix, const uint8
                                                 uint32_t Lstep = 1) {
     const uint32_t curves = ix.P.curves;
     uint64_t khi = 0, klo = 0;
-    if ((uint32_t)lane < curves) curve_key(qrow, ix.P, (uint32_t)lane, khi, klo);
+    if ((uint32_t)lane < curves) curve_key_call(qrow, ix.P, (uint32_t)lane, khi, klo);
     const uint32_t mine = (ix.lists > L0) ? (ix.lists - L0 + Lstep - 1) / Lstep : 0;
     for (uint32_t b = 0; b < mine; b += 32) {
         const uint32_t t = b + (uint32_t)lane;
@@ -346,7 +346,8 @@ __device__ __forceinline__ void search_lists_staged(const IndexView& ix, const u
     const uint32_t s = (uint32_t)lane % LPR;
     const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
     const uint8_t* db = static_cast<const uint8_t*>(ix.db);
-    const uint32_t stage_bytes = 32 * ix.row_bytes;
+    const uint32_t row_bytes = ix.row_bytes;
+    const uint32_t stage_bytes = 32 * row_bytes;
     const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
 
     // first non-empty window: step A
@@ -357,7 +358,7 @@ __device__ __forceinline__ void search_lists_staged(const IndexView& ix, const u
     }
     if (aL >= ix.lists) return;
     uint32_t aid = step_ids(ix, aL, abase, ahi, lane);
-    issue_step(db, ix.row_bytes, ring_s, aid, min(32u, ahi - abase), lane);
+    issue_step(db, row_bytes, ring_s, aid, min(32u, ahi - abase), lane);
     cp_async_commit();
     // step B after A
     uint32_t bL = aL, bbase = abase, bhi = ahi;
@@ -366,7 +367,7 @@ __device__ __forceinline__ void search_lists_staged(const IndexView& ix, const u
     uint32_t st = 0;
     while (true) {
         if (hb)
-            issue_step(db, ix.row_bytes, ring_s + (st ^ 1u) * stage_bytes, bid,
+            issue_step(db, row_bytes, ring_s + (st ^ 1u) * stage_bytes, bid,
                        min(32u, bhi - bbase), lane);
         cp_async_commit();
         // step C after B: its ids
@@ -375,7 +376,7 @@ __device__ __forceinline__ void search_lists_staged(const IndexView& ix, const u
         const uint32_t cid = hc ? step_ids(ix, cL, cbase, chi, lane) : 0u;
         cp_async_wait<1>();   // step A has landed
         __syncwarp();
-        top.offer(staged_candidates<F32, LPR>(ring + st * stage_bytes, ix.row_bytes, qv0, aid,
+        top.offer(staged_candidates<F32, LPR>(ring + st * stage_bytes, row_bytes, qv0, aid,
                                               min(32u, ahi - abase), lane),
                   k, lane);
         __syncwarp();         // every lane is done with stage st before it is refilled

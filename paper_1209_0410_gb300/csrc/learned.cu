@@ -413,7 +413,7 @@ __device__ __forceinline__ void warp_keys_positions(const IndexView& ix, const u
     khi = 0;
     klo = 0;
     const uint32_t curves = ix.P.curves;
-    if ((uint32_t)lane < curves) curve_key(qrow, ix.P, (uint32_t)lane, khi, klo);
+    if ((uint32_t)lane < curves) curve_key_call(qrow, ix.P, (uint32_t)lane, khi, klo);
     if ((uint32_t)lane < curves) {
         const uint64_t off = ix.list_off[lane];
         const uint32_t n = (uint32_t)(ix.list_off[lane + 1] - off);

@@ -107,9 +107,9 @@ __device__ __forceinline__ void run_variant(const MultiJob& J, uint32_t qi, bool
     multi_query<F32, LPR, KR>(J, qi, active, sub, pos_w, mb, ring, lane);
 }
 
-__global__ void multi_kernel(const MultiJob* __restrict__ jobs, const MultiTask* __restrict__ tasks,
-                             uint32_t ntasks, uint32_t tile, uint32_t* __restrict__ counter,
-                             bool staged) {
+__global__ void __launch_bounds__(kMaxWarps * 32)
+    multi_kernel(const MultiJob* __restrict__ jobs, const MultiTask* __restrict__ tasks,
+                 uint32_t ntasks, uint32_t tile, uint32_t* __restrict__ counter, bool staged) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t nwarps = blockDim.x >> 5;
     uint64_t* merge = reinterpret_cast<uint64_t*>(smem_raw);             // nwarps x 4 x 32

@@ -1,5 +1,6 @@
-// K3..K6: the fused query kernel (Algorithm 2 for a batch of queries) and the
-// exact brute-force kNN (Eq. 3) that shares its distance and top-k code.
+// K3..K6: the fused query kernel (Algorithm 2 for a batch of queries); the
+// exact brute-force kNN (Eq. 3), which shares its distance and top-k code,
+// is in brute.cu.
 //
 // One warp per query:
 //   K1  lanes c < curves compute the query's extended-key on curve c;
@@ -23,6 +24,7 @@
 // The path is a gather bounded by HBM bandwidth; no tensor cores are used.
 #include <algorithm>
 
+#include "hc_dispatch.cuh"
 #include "hc_internal.h"
 #include "hc_query_dev.cuh"
 #include "hc_topk.cuh"
@@ -65,9 +67,9 @@ __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kerne
     if constexpr (STAGED) {
         uint8_t* ring = reinterpret_cast<uint8_t*>(s_pos + kQWarps * ix.lists) +
                         (size_t)warp * 64 * ix.row_bytes;
-        search_lists_staged<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists,
-                                          ring, top, lane,
-                                          a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
+        search_lists_staged<F32, LPR, KR>(
+            ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, ring, top, lane,
+            a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
     } else {
         search_lists<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, top,
                                    lane, a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
@@ -88,91 +90,30 @@ __global__ void __launch_bounds__(kQWarps * 32) positions_kernel(QueryArgs a) {
         a.out_pos[(size_t)qi * a.ix.lists + L] = (int64_t)pos_w[L];
 }
 
-// Exact kNN: every row of the database, 32 rows per step, same distance and
-// top-k code as the query kernel.
-template <bool F32, int LPR, int KR>
-__global__ void __launch_bounds__(kQWarps * 32) brute_kernel(const uint8_t* __restrict__ db,
-                                                            uint64_t n, uint32_t row_bytes,
-                                                            const uint8_t* __restrict__ q,
-                                                            uint32_t nq, uint32_t k,
-                                                            int32_t* out_ids, void* out_dist) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t qi = blockIdx.x * kQWarps + warp;
-    if (qi >= nq) return;
-    const uint8_t* qrow = q + (size_t)qi * row_bytes;
-    const uint32_t s = (uint32_t)lane % LPR;
-    const uint4 qv0 = s < (row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
-    WarpTopK<KR> top;
-    top.init();
-    for (uint64_t base = 0; base < n; base += 32) {
-        const uint32_t cnt = n - base < 32 ? (uint32_t)(n - base) : 32u;
-        const uint32_t id = (uint32_t)(base + lane);
-        uint64_t cand[ChunkWidth<LPR>::NG];
-        chunk_candidates_n<F32, LPR>(db, row_bytes, qrow, qv0, id, cnt, lane, cand);
-#pragma unroll
-        for (int c = 0; c < ChunkWidth<LPR>::NG; ++c) top.offer(cand[c], k, lane);
-    }
-    top.template store<F32>(k, lane, out_ids + (size_t)qi * k,
-                            static_cast<uint32_t*>(out_dist) + (size_t)qi * k);
-}
-
-int lanes_per_row(uint32_t row_bytes) {
-    const uint32_t vecs = row_bytes / 16;
-    if (vecs <= 4) return 4;
-    if (vecs <= 8) return 8;
-    if (vecs <= 16) return 16;
-    return 32;
-}
-
-int regs_for_k(uint32_t k) { return k <= 32 ? 1 : (k <= 64 ? 2 : 4); }
-
-// dispatch on (dtype, lanes per row, top-k registers)
-template <template <bool, int, int> class Launch, typename... Args>
-cudaError_t dispatch(bool f32, int lpr, int kr, Args... args) {
-#define HC_CASE(F, L, K)                                   \
-    if (f32 == F && lpr == L && kr == K) return Launch<F, L, K>::run(args...);
-#define HC_CASES_L(F, L) HC_CASE(F, L, 1) HC_CASE(F, L, 2) HC_CASE(F, L, 4)
-#define HC_CASES_F(F) HC_CASES_L(F, 4) HC_CASES_L(F, 8) HC_CASES_L(F, 16) HC_CASES_L(F, 32)
-    HC_CASES_F(false)
-    HC_CASES_F(true)
-#undef HC_CASES_F
-#undef HC_CASES_L
-#undef HC_CASE
-    return cudaErrorInvalidValue;
-}
-
 template <bool F32, int LPR, int KR>
 struct QueryLaunch {
-    static cudaError_t run(const QueryArgs& a, cudaStream_t s) {
+    template <bool STAGED>
+    static cudaError_t go(const QueryArgs& a, size_t smem, cudaStream_t s) {
         const unsigned blocks = (a.nq + kQWarps - 1) / kQWarps;
-        const size_t pos_bytes = sizeof(uint32_t) * kQWarps * a.ix.lists;
-        if constexpr (LPR <= 8) {
-            if (a.ix.row_bytes <= 128) {
-                const size_t smem = pos_bytes + (size_t)kQWarps * 64 * a.ix.row_bytes;
-                cudaError_t e = cudaFuncSetAttribute(query_kernel<F32, LPR, KR, true>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)smem);
-                if (e != cudaSuccess) return e;
-                query_kernel<F32, LPR, KR, true><<<blocks, kQWarps * 32, smem, s>>>(a);
-                count_launches(1);
-                return cudaGetLastError();
-            }
+        if (STAGED) {
+            cudaError_t e = cudaFuncSetAttribute(query_kernel<F32, LPR, KR, STAGED>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
         }
-        query_kernel<F32, LPR, KR, false><<<blocks, kQWarps * 32, pos_bytes, s>>>(a);
+        query_kernel<F32, LPR, KR, STAGED><<<blocks, kQWarps * 32, smem, s>>>(a);
         count_launches(1);
         return cudaGetLastError();
     }
-};
-
-template <bool F32, int LPR, int KR>
-struct BruteLaunch {
-    static cudaError_t run(const uint8_t* db, uint64_t n, uint32_t row_bytes, const uint8_t* q,
-                           uint32_t nq, uint32_t k, int32_t* ids, void* dist, cudaStream_t s) {
-        const unsigned blocks = (nq + kQWarps - 1) / kQWarps;
-        brute_kernel<F32, LPR, KR><<<blocks, kQWarps * 32, 0, s>>>(db, n, row_bytes, q, nq, k,
-                                                                   ids, dist);
-        count_launches(1);
-        return cudaGetLastError();
+    static cudaError_t run(const QueryArgs& a, cudaStream_t s) {
+        const size_t pos_bytes = sizeof(uint32_t) * kQWarps * a.ix.lists;
+        // rows of at most 128 bytes (all rows of 4 or 8 lanes) are staged
+        if constexpr (LPR <= 8) {
+            const size_t smem = pos_bytes + (size_t)kQWarps * 64 * a.ix.row_bytes;
+            return go<true>(a, smem, s);
+        } else {
+            return go<false>(a, pos_bytes, s);
+        }
     }
 };
 
@@ -195,16 +136,6 @@ cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, in
     positions_kernel<<<blocks, kQWarps * 32, sizeof(uint32_t) * kQWarps * ix.lists, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
-}
-
-cudaError_t launch_bruteforce(const void* db, hc_dtype dtype, uint64_t n, uint32_t d,
-                              const void* q, uint32_t nq, uint32_t k, int32_t* out_ids,
-                              void* out_dist, cudaStream_t s) {
-    if (nq == 0) return cudaSuccess;
-    const uint32_t row_bytes = dtype == HC_F32 ? d * 4 : d;
-    return dispatch<BruteLaunch>(dtype == HC_F32, lanes_per_row(row_bytes), regs_for_k(k),
-                                 static_cast<const uint8_t*>(db), n, row_bytes,
-                                 static_cast<const uint8_t*>(q), nq, k, out_ids, out_dist, s);
 }
 
 }  // namespace hc
