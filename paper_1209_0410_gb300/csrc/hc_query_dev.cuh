@@ -242,12 +242,13 @@ __device__ __forceinline__ void search_lists(const IndexView& ix, const uint8_t*
 
 // ---------------------------------------------------------------------------
 // Staged form of the window walk for rows of at most 128 bytes (one 16-byte
-// vector per lane of a row group, LPR <= 8): the rows of the next 32-entry
-// step are copied into a per-warp shared-memory ring with cp.async (no
-// registers held while they are in flight) while the current step's rows are
-// reduced, and the step after that has its ids loaded.  The steps run over
-// all windows of the query back to back, so the copies do not drain at
-// window ends.  Waits are the hardware's cp.async group waits.
+// vector per lane of a row group, LPR <= 8): the windows of all lists are
+// packed back to back and walked in steps of 32 entries (a step may span
+// several short windows, so short or uneven windows fill whole steps); the
+// rows of the next step are copied into a per-warp shared-memory ring with
+// cp.async (no registers held while they are in flight) while the current
+// step's rows are reduced, and the step after that has its ids loaded.
+// Waits are the hardware's cp.async group waits.
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
 }
@@ -259,34 +260,63 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// window [lo, hi) of list L around position pos_w[L]
-__device__ __forceinline__ void window_of(const IndexView& ix, const uint32_t* pos_w,
-                                          uint32_t depth, uint32_t L, uint32_t& lo,
-                                          uint32_t& hi) {
-    const uint32_t n = (uint32_t)(ix.list_off[L + 1] - ix.list_off[L]);
-    const uint32_t pos = pos_w[L];
-    lo = pos > depth ? pos - depth : 0u;
-    hi = (uint64_t)pos + depth < (uint64_t)n ? pos + depth : n;
-}
-
-// the step after (L, base) in the walk over lists L0, L0 + Lstep, ...;
-// false when the walk is over
-__device__ __forceinline__ bool next_step(const IndexView& ix, const uint32_t* pos_w,
-                                          uint32_t depth, uint32_t Lstep, uint32_t& L,
-                                          uint32_t& base, uint32_t& hi) {
-    base += 32;
-    while (base >= hi) {
-        L += Lstep;
-        if (L >= ix.lists) return false;
-        window_of(ix, pos_w, depth, L, base, hi);
+// The windows of the lists this warp walks (L = L0 + m Lstep), packed back
+// to back: win_at[m] = first ids entry of window m (global entry index),
+// win_pre[m] = number of window entries before window m.  Returns the total.
+// win_at may alias pos_w (each slot is read before it is written).
+__device__ __forceinline__ uint32_t pack_windows(const IndexView& ix, uint32_t depth, uint32_t L0,
+                                                 uint32_t Lstep, const uint32_t* pos_w,
+                                                 uint32_t* win_at, uint32_t* win_pre, int lane) {
+    const uint32_t nm = ix.lists > L0 ? (ix.lists - L0 + Lstep - 1) / Lstep : 0;
+    uint32_t carry = 0;
+    for (uint32_t b = 0; b < nm; b += 32) {
+        const uint32_t m = b + (uint32_t)lane;
+        uint32_t len = 0, at = 0;
+        if (m < nm) {
+            const uint32_t L = L0 + m * Lstep;
+            const uint64_t off = ix.list_off[L];
+            const uint32_t n = (uint32_t)(ix.list_off[L + 1] - off);
+            const uint32_t pos = pos_w[L];
+            const uint32_t lo = pos > depth ? pos - depth : 0u;
+            const uint32_t hi = (uint64_t)pos + depth < (uint64_t)n ? pos + depth : n;
+            len = hi > lo ? hi - lo : 0u;
+            at = (uint32_t)(off + lo);   // index entries < 2^32
+        }
+        uint32_t x = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        __syncwarp();
+        if (m < nm) {
+            win_at[m] = at;
+            win_pre[m] = carry + x - len;
+        }
+        carry += __shfl_sync(0xffffffffu, x, 31);
     }
-    return true;
+    __syncwarp();
+    return carry;
 }
 
-__device__ __forceinline__ uint32_t step_ids(const IndexView& ix, uint32_t L, uint32_t base,
-                                             uint32_t hi, int lane) {
-    const uint32_t e = base + (uint32_t)lane;
-    return e < hi ? __ldg(ix.ids + ix.list_off[L] + e) : 0u;
+// ids of packed step s (entries 32 s .. 32 s + 31 of the concatenated
+// windows): lane l finds its window by binary search over win_pre
+__device__ __forceinline__ uint32_t packed_ids(const IndexView& ix, const uint32_t* win_at,
+                                               const uint32_t* win_pre, uint32_t nm,
+                                               uint32_t total, uint32_t s, int lane) {
+    const uint32_t e = 32 * s + (uint32_t)lane;
+    if (e >= total) return 0u;
+    uint32_t lo = 0, count = nm;   // largest m with win_pre[m] <= e
+    while (count > 1) {
+        const uint32_t half = count >> 1;
+        if (win_pre[lo + half] <= e) {
+            lo += half;
+            count -= half;
+        } else {
+            count = half;
+        }
+    }
+    return __ldg(ix.ids + win_at[lo] + (e - win_pre[lo]));
 }
 
 // copies of one step: lane (c = lane % 8, g = lane / 8) moves vector c of
@@ -334,7 +364,8 @@ template <bool F32, int LPR, int KR>
 __device__ __forceinline__ void search_lists_staged(const IndexView& ix, const uint8_t* qrow,
                                                     uint32_t depth, uint32_t k, uint32_t L0,
                                                     uint32_t Lstep, uint32_t* pos_w,
-                                                    uint8_t* ring, WarpTopK<KR>& top, int lane,
+                                                    uint32_t* win_pre, uint8_t* ring,
+                                                    WarpTopK<KR>& top, int lane,
                                                     const int64_t* pos_in = nullptr) {
     if (pos_in) {
         for (uint32_t L = L0 + (uint32_t)lane * Lstep; L < ix.lists; L += 32 * Lstep)
@@ -349,46 +380,32 @@ __device__ __forceinline__ void search_lists_staged(const IndexView& ix, const u
     const uint32_t row_bytes = ix.row_bytes;
     const uint32_t stage_bytes = 32 * row_bytes;
     const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
-
-    // first non-empty window: step A
-    uint32_t aL = L0, abase = 0, ahi = 0;
-    for (; aL < ix.lists; aL += Lstep) {
-        window_of(ix, pos_w, depth, aL, abase, ahi);
-        if (abase < ahi) break;
-    }
-    if (aL >= ix.lists) return;
-    uint32_t aid = step_ids(ix, aL, abase, ahi, lane);
-    issue_step(db, row_bytes, ring_s, aid, min(32u, ahi - abase), lane);
+    const uint32_t nm = ix.lists > L0 ? (ix.lists - L0 + Lstep - 1) / Lstep : 0;
+    uint32_t* win_at = pos_w;   // positions are consumed by pack_windows
+    const uint32_t total = pack_windows(ix, depth, L0, Lstep, pos_w, win_at, win_pre, lane);
+    const uint32_t steps = (total + 31) / 32;
+    if (steps == 0) return;
+    // step A = 0 copied, step B = 1 ids loaded
+    uint32_t aid = packed_ids(ix, win_at, win_pre, nm, total, 0, lane);
+    issue_step(db, row_bytes, ring_s, aid, min(32u, total), lane);
     cp_async_commit();
-    // step B after A
-    uint32_t bL = aL, bbase = abase, bhi = ahi;
-    bool hb = next_step(ix, pos_w, depth, Lstep, bL, bbase, bhi);
-    uint32_t bid = hb ? step_ids(ix, bL, bbase, bhi, lane) : 0u;
+    uint32_t bid = steps > 1 ? packed_ids(ix, win_at, win_pre, nm, total, 1, lane) : 0u;
     uint32_t st = 0;
-    while (true) {
-        if (hb)
+    for (uint32_t a = 0; a < steps; ++a) {
+        if (a + 1 < steps)
             issue_step(db, row_bytes, ring_s + (st ^ 1u) * stage_bytes, bid,
-                       min(32u, bhi - bbase), lane);
+                       min(32u, total - 32 * (a + 1)), lane);
         cp_async_commit();
-        // step C after B: its ids
-        uint32_t cL = bL, cbase = bbase, chi = bhi;
-        const bool hc = hb && next_step(ix, pos_w, depth, Lstep, cL, cbase, chi);
-        const uint32_t cid = hc ? step_ids(ix, cL, cbase, chi, lane) : 0u;
-        cp_async_wait<1>();   // step A has landed
+        const uint32_t cid = a + 2 < steps ? packed_ids(ix, win_at, win_pre, nm, total, a + 2, lane)
+                                           : 0u;
+        cp_async_wait<1>();   // step a has landed
         __syncwarp();
         top.offer(staged_candidates<F32, LPR>(ring + st * stage_bytes, row_bytes, qv0, aid,
-                                              min(32u, ahi - abase), lane),
+                                              min(32u, total - 32 * a), lane),
                   k, lane);
         __syncwarp();         // every lane is done with stage st before it is refilled
-        if (!hb) break;
         aid = bid;
-        abase = bbase;
-        ahi = bhi;
-        bL = cL;
-        bbase = cbase;
-        bhi = chi;
         bid = cid;
-        hb = hc;
         st ^= 1u;
     }
     cp_async_wait<0>();

@@ -70,8 +70,8 @@ __device__ void multi_query(const MultiJob& J, uint32_t qi, bool active, uint32_
         const uint8_t* qrow = J.q + (size_t)qi * J.ix.row_bytes;
         if constexpr (LPR <= 8) {
             if (ring && J.ix.row_bytes <= 128) {
-                search_lists_staged<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w, ring,
-                                                  top, lane);
+                search_lists_staged<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w,
+                                                  pos_w + kMaxLists, ring, top, lane);
             } else {
                 search_lists<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w, top, lane);
             }
@@ -113,8 +113,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t nwarps = blockDim.x >> 5;
     uint64_t* merge = reinterpret_cast<uint64_t*>(smem_raw);             // nwarps x 4 x 32
-    uint32_t* pos = reinterpret_cast<uint32_t*>(merge + nwarps * 4 * 32); // nwarps x kMaxLists
-    uint8_t* rings = reinterpret_cast<uint8_t*>(pos + nwarps * kMaxLists); // nwarps x kRingBytes
+    // per warp: kMaxLists positions, then kMaxLists window prefixes
+    uint32_t* pos = reinterpret_cast<uint32_t*>(merge + nwarps * 4 * 32);
+    uint8_t* rings = reinterpret_cast<uint8_t*>(pos + nwarps * 2 * kMaxLists); // nwarps x kRingBytes
     __shared__ uint32_t s_task;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = threadIdx.x >> 5;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
             const uint32_t qo = rep * per_pass + group;
             const bool active = group < per_pass && qo < T.cnt;
             const uint32_t qi = T.q0 + qo;
-            uint32_t* pw = pos + (size_t)warp * kMaxLists;
+            uint32_t* pw = pos + (size_t)warp * 2 * kMaxLists;
             uint8_t* ring = staged ? rings + (size_t)warp * kRingBytes : nullptr;
             switch (J.variant) {
 #define HC_V(n) \
@@ -152,7 +153,7 @@ __global__ void reset_counter_kernel(uint32_t* c) { *c = 0; }
 
 size_t multi_smem(uint32_t nwarps, bool staged) {
     return (size_t)nwarps * 4 * 32 * sizeof(uint64_t) +
-           (size_t)nwarps * kMaxLists * sizeof(uint32_t) + (staged ? nwarps * kRingBytes : 0);
+           (size_t)nwarps * 2 * kMaxLists * sizeof(uint32_t) + (staged ? nwarps * kRingBytes : 0);
 }
 
 }  // namespace

@@ -52,7 +52,8 @@ struct QueryArgs {
 #endif
 
 // STAGED: rows of at most 128 bytes go through a two-step cp.async ring in
-// shared memory (kQWarps x 2 x 32 rows after the positions)
+// shared memory (kQWarps x 2 x 32 rows after the positions and the window
+// prefixes)
 template <bool F32, int LPR, int KR, bool STAGED>
 __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kernel(QueryArgs a) {
     extern __shared__ __align__(16) uint32_t s_pos[];  // kQWarps x lists, then the rings
@@ -65,11 +66,13 @@ __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kerne
     WarpTopK<KR> top;
     top.init();
     if constexpr (STAGED) {
-        uint8_t* ring = reinterpret_cast<uint8_t*>(s_pos + kQWarps * ix.lists) +
+        // after the positions: kQWarps x lists window prefixes, then the rings
+        uint32_t* s_pre = s_pos + kQWarps * ix.lists;
+        uint8_t* ring = reinterpret_cast<uint8_t*>(s_pre + kQWarps * ix.lists) +
                         (size_t)warp * 64 * ix.row_bytes;
         search_lists_staged<F32, LPR, KR>(
-            ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, ring, top, lane,
-            a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
+            ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, s_pre + warp * ix.lists, ring,
+            top, lane, a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
     } else {
         search_lists<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, top,
                                    lane, a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
@@ -109,7 +112,7 @@ struct QueryLaunch {
         const size_t pos_bytes = sizeof(uint32_t) * kQWarps * a.ix.lists;
         // rows of at most 128 bytes (all rows of 4 or 8 lanes) are staged
         if constexpr (LPR <= 8) {
-            const size_t smem = pos_bytes + (size_t)kQWarps * 64 * a.ix.row_bytes;
+            const size_t smem = 2 * pos_bytes + (size_t)kQWarps * 64 * a.ix.row_bytes;
             return go<true>(a, smem, s);
         } else {
             return go<false>(a, pos_bytes, s);
