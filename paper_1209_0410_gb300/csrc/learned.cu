@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kPredWarps * 32) mlp_infer_kernel(MlpView V,
 size_t pred_smem(const MlpView& V) {
     const uint32_t nw = V.in * V.h1 + V.h1 * V.h2 + V.h2;
     return ((nw * 2 + 15) & ~15u) + sizeof(float) * (4 * kMaxDim + 1 + 3) +
-           sizeof(float) * kPredWarps * 2 * kMaxDim + sizeof(uint32_t) * kPredWarps * 64;
+           sizeof(float) * kPredWarps * 2 * kMaxDim + sizeof(uint32_t) * kPredWarps * (64 + 128);
 }
 
 // ------------------------------------------------------------ features
@@ -350,59 +350,92 @@ __device__ __forceinline__ float octave128(uint64_t hi, uint64_t lo) {
 
 constexpr float kFeatNone = 130.0f;
 
+// 128-bit gap (a - b) of two keys, octave-encoded
+__device__ __forceinline__ float key_gap_octave(uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl) {
+    const uint64_t gl = al - bl, gh = ah - bh - (al < bl ? 1u : 0u);
+    return octave128(gh, gl);
+}
+
 // The 4 * curves features of one query into xs (warp-shared), from the
-// positions pos_w of lists 0..curves-1.  khi/klo: lane c holds curve c's key.
+// positions pos_w of lists 0..curves-1 (khi/klo: lane c holds curve c's key).
+// All curves at once: the 8-entry centre windows fill 32-row steps (slot
+// 8 c + j = entry j of curve c's window, distances parked in sd), and lanes
+// 2 c, 2 c + 1 take curve c's predecessor and successor gaps (a low key word
+// recomputed from its row where the index keeps high words only).
 __device__ void query_features(const IndexView& ix, const uint8_t* qrow, uint4 qv0,
                                const uint32_t* pos_w, uint64_t khi, uint64_t klo, float* xs,
-                               int lane) {
+                               uint32_t* sd, int lane) {
     const uint8_t* db = static_cast<const uint8_t*>(ix.db);
-    for (uint32_t c = 0; c < ix.P.curves; ++c) {
-        const uint64_t off = ix.list_off[c];
-        const uint32_t n = (uint32_t)(ix.list_off[c + 1] - off);
-        const uint32_t pos = pos_w[c];
-        const uint32_t lo = pos > 4 ? pos - 4 : 0u, hi = pos + 4 < n ? pos + 4 : n;
-        const uint32_t cnt = hi - lo;
-        const uint32_t id = (uint32_t)lane < cnt ? __ldg(ix.ids + off + lo + lane) : 0u;
+    const uint32_t C = ix.P.curves;
+    // centre window of curve c = lane / 8 (per slot)
+    for (uint32_t t = 0; t < C; t += 4) {
+        const uint32_t c = t + (uint32_t)lane / 8, j = (uint32_t)lane % 8;
+        uint32_t id = 0;
+        bool valid = false;
+        if (c < C) {
+            const uint64_t off = ix.list_off[c];
+            const uint32_t n = (uint32_t)(ix.list_off[c + 1] - off);
+            const uint32_t pos = pos_w[c];
+            const uint32_t lo = pos > 4 ? pos - 4 : 0u, hi = pos + 4 < n ? pos + 4 : n;
+            valid = lo + j < hi;
+            if (valid) id = __ldg(ix.ids + off + lo + j);
+        }
         uint64_t cands[ChunkWidth<8>::NG];
-        chunk_candidates_n<false, 8>(db, ix.row_bytes, qrow, qv0, id, cnt, lane, cands);
-        uint32_t dmin = 0xFFFFFFFFu;
+        chunk_candidates_n<false, 8>(db, ix.row_bytes, qrow, qv0, id, 32u, lane, cands);
+        // lane l holds the row (l % 8) * 4 + l / 8 of the step
+        const uint32_t r = ((uint32_t)lane % 8) * 4 + (uint32_t)lane / 8;
+        const bool rvalid = __shfl_sync(0xffffffffu, valid, (int)r);
+        sd[8 * t + r] = rvalid ? (uint32_t)(cands[0] >> 32) : 0xFFFFFFFFu;
+    }
+    __syncwarp();
+    float f0 = kFeatNone, f1 = kFeatNone, f2 = kFeatNone, f3 = kFeatNone;
+    {
+        // lanes 2c, 2c+1: predecessor / successor gap of curve c
+        const uint32_t c = (uint32_t)lane / 2;
+        const uint64_t kh = __shfl_sync(0xffffffffu, khi, (int)(c < C ? c : 0));
+        const uint64_t kl = __shfl_sync(0xffffffffu, klo, (int)(c < C ? c : 0));
+        float gap = kFeatNone;
+        if (c < C) {
+            const uint64_t off = ix.list_off[c];
+            const uint32_t n = (uint32_t)(ix.list_off[c + 1] - off);
+            const uint32_t pos = pos_w[c];
+            if ((lane & 1) == 0 && pos > 0) {
+                const uint64_t g = off + pos - 1;
+                gap = key_gap_octave(kh, kl, ix.keys_hi[g], entry_key_lo(ix, c, g));
+            } else if ((lane & 1) == 1 && pos < n) {
+                const uint64_t g = off + pos;
+                gap = key_gap_octave(ix.keys_hi[g], entry_key_lo(ix, c, g), kh, kl);
+            }
+        }
+        const float other = __shfl_xor_sync(0xffffffffu, gap, 1);
+        f0 = (lane & 1) ? other : gap;
+        f1 = (lane & 1) ? gap : other;
+    }
+    if ((uint32_t)lane < C) {
+        // centre-window distances of curve lane
+        uint32_t dmin = 0xFFFFFFFFu, cnt = 0;
         uint64_t dsum = 0;
-#pragma unroll
-        for (int g = 0; g < ChunkWidth<8>::NG; ++g)
-            if (cands[g] != kEmpty) {
-                dmin = min(dmin, (uint32_t)(cands[g] >> 32));
-                dsum += cands[g] >> 32;
+        for (uint32_t j = 0; j < 8; ++j) {
+            const uint32_t v = sd[8 * lane + j];
+            if (v != 0xFFFFFFFFu) {
+                dmin = min(dmin, v);
+                dsum += v;
+                ++cnt;
             }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
-            dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
         }
-        const uint64_t kh = __shfl_sync(0xffffffffu, khi, (int)c);
-        const uint64_t kl = __shfl_sync(0xffffffffu, klo, (int)c);
-        if (lane == 0) {
-            float f0 = kFeatNone, f1 = kFeatNone, f2 = kFeatNone, f3 = kFeatNone;
-            if (pos > 0) {
-                const uint64_t ph = ix.keys_hi[off + pos - 1];
-                const uint64_t pl = entry_key_lo(ix, c, off + pos - 1);
-                const uint64_t gl = kl - pl, gh = kh - ph - (kl < pl ? 1u : 0u);
-                f0 = octave128(gh, gl);
-            }
-            if (pos < n) {
-                const uint64_t nh = ix.keys_hi[off + pos];
-                const uint64_t nl = entry_key_lo(ix, c, off + pos);
-                const uint64_t gl = nl - kl, gh = nh - kh - (nl < kl ? 1u : 0u);
-                f1 = octave128(gh, gl);
-            }
-            if (cnt) {
-                f2 = octave128(0, dmin);
-                f3 = octave128(0, dsum / cnt);
-            }
-            xs[4 * c + 0] = f0;
-            xs[4 * c + 1] = f1;
-            xs[4 * c + 2] = f2;
-            xs[4 * c + 3] = f3;
+        if (cnt) {
+            f2 = octave128(0, dmin);
+            f3 = octave128(0, dsum / cnt);
         }
+    }
+    // lane c < C gathers its curve's gap pair from lane 2c
+    const float g0 = __shfl_sync(0xffffffffu, f0, (2 * lane) & 31);
+    const float g1 = __shfl_sync(0xffffffffu, f1, (2 * lane) & 31);
+    if ((uint32_t)lane < C) {
+        xs[4 * lane + 0] = g0;
+        xs[4 * lane + 1] = g1;
+        xs[4 * lane + 2] = f2;
+        xs[4 * lane + 3] = f3;
     }
     __syncwarp();
 }
@@ -424,7 +457,7 @@ __device__ __forceinline__ void warp_keys_positions(const IndexView& ix, const u
 
 __global__ void __launch_bounds__(kPredWarps * 32) features_kernel(IndexView ix, const uint8_t* q,
                                                                    uint32_t nq, float* feat) {
-    __shared__ uint32_t s_pos[kPredWarps][64];
+    __shared__ uint32_t s_pos[kPredWarps][64 + 128];   // positions, then window distances
     __shared__ float s_x[kPredWarps][4 * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t qi = blockIdx.x * kPredWarps + warp;
@@ -434,13 +467,13 @@ __global__ void __launch_bounds__(kPredWarps * 32) features_kernel(IndexView ix,
     warp_keys_positions(ix, qrow, s_pos[warp], khi, klo, lane);
     const uint32_t s = (uint32_t)lane % 8;
     const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
-    query_features(ix, qrow, qv0, s_pos[warp], khi, klo, s_x[warp], lane);
+    query_features(ix, qrow, qv0, s_pos[warp], khi, klo, s_x[warp], s_pos[warp] + 64, lane);
     for (uint32_t j = lane; j < 4 * ix.P.curves; j += 32)
         feat[(size_t)qi * 4 * ix.P.curves + j] = s_x[warp][j];
 }
 
 // features -> MLP -> p = clamp(ceil(2^(y + margin)), p_lo, p_hi), per query
-__global__ void __launch_bounds__(kPredWarps * 32) predict_depths_kernel(
+__global__ void __launch_bounds__(kPredWarps * 32, 4) predict_depths_kernel(
     IndexView ix, MlpView V, const uint8_t* q, uint32_t nq, float margin, uint32_t p_lo,
     uint32_t p_hi, uint32_t* p_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -453,14 +486,14 @@ __global__ void __launch_bounds__(kPredWarps * 32) predict_depths_kernel(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* xs = sx + warp * 2 * kMaxDim;
     float* hs = xs + kMaxDim;
-    uint32_t* pos_w = spos + warp * 64;
+    uint32_t* pos_w = spos + warp * (64 + 128);
     for (uint32_t qi = blockIdx.x * kPredWarps + warp; qi < nq; qi += gridDim.x * kPredWarps) {
         const uint8_t* qrow = q + (size_t)qi * ix.row_bytes;
         uint64_t khi, klo;
         warp_keys_positions(ix, qrow, pos_w, khi, klo, lane);
         const uint32_t s = (uint32_t)lane % 8;
         const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
-        query_features(ix, qrow, qv0, pos_w, khi, klo, xs, lane);
+        query_features(ix, qrow, qv0, pos_w, khi, klo, xs, pos_w + 64, lane);
         const float y = mlp_warp_forward(V, sW, sW + V.in * V.h1, sW + V.in * V.h1 + V.h1 * V.h2,
                                          sb, xs, hs, lane);
         if (lane == 0) {
