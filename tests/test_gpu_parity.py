@@ -329,6 +329,33 @@ def test_query_host_matches_device(hc):
         assert np.array_equal(ids_h.numpy(), rids[:m])
 
 
+@pytest.mark.parametrize("parts", [1, 3])
+def test_build_host_from_pinned_rows(hc, parts):
+    """hc_build_host from pinned host rows: the lists equal those of a build
+    from device memory, and a full-depth query (every row of the library's
+    device copy) is the exact kNN."""
+    import torch
+    n, nq = 20011, 97
+    db, q = make_case(n, nq, seed=29)
+    pinned = torch.from_numpy(db).pin_memory()
+    idx_h = hc.hc_build_host(pinned, partitions=parts)
+    idx_d = hc.hc_build(dev(db), partitions=parts)
+    a = hc.hc_index_copy_lists(idx_h)
+    b = hc.hc_index_copy_lists(idx_d)
+    sync()
+    for x, y in zip(a[:3], b[:3]):
+        assert torch.equal(x, y)
+    ids_h, dist_h = hc.hc_query_host(idx_h, q, 10, 40)
+    oidx = O.build(db, curves=8, m=16, ell=parts)
+    rids, rdist = O.search(oidx, db, q, 10, 40)
+    assert np.array_equal(ids_h.numpy(), rids)
+    assert np.array_equal(dist_h.numpy(), O.int32_dist(rdist))
+    ids_f, dist_f = hc.hc_query_host(idx_h, q[:20], 10, n)
+    fids, fdist = O.bruteforce(db, q[:20], 10)
+    assert np.array_equal(ids_f.numpy(), fids)
+    assert np.array_equal(dist_f.numpy(), O.int32_dist(fdist))
+
+
 # ------------------------------------------------------------- exact kNN
 @pytest.mark.parametrize("dtype,k,d", [("u8", 10, 128), ("u8", 100, 128), ("u8", 1, 64),
                                        ("f32", 10, 128), ("f32", 33, 256), ("u8", 128, 32)])
