@@ -42,7 +42,8 @@ DATA = ("synthetic: seeded 64-cluster isotropic Gaussian mixture (centres unifor
         "[0,255], sigma 20, rounded and clipped) standing in for 128-d SIFT; queries are "
         "database rows plus N(0, 8) noise")
 QUERY_SOURCES = ["paper_1209_0410_gb300/csrc/query.cu", "paper_1209_0410_gb300/csrc/hc_topk.cuh",
-                 "paper_1209_0410_gb300/csrc/hc_device.cuh"]
+                 "paper_1209_0410_gb300/csrc/hc_device.cuh",
+                 "paper_1209_0410_gb300/csrc/hc_query_dev.cuh"]
 
 
 def parse_args():
