@@ -409,48 +409,65 @@ __global__ void __launch_bounds__(256) fixup_runs_kernel(uint64_t* hi, uint32_t*
     const uint32_t curve = seg % rows.P.curves;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (uint32_t base = warp * 32; base < count; base += nwarps * 32) {
-        const uint64_t i = start + base + lane;
-        bool run_start = false;
-        if (base + lane < count && i + 1 < seg_end) {
-            const uint64_t key = hi[i] >> run_shift;
-            run_start = (hi[i + 1] >> run_shift) == key &&
-                        !(i > si.start && (hi[i - 1] >> run_shift) == key);
+    // kBatch chunks of 32 records per warp have their words loaded at once
+    constexpr int kBatch = 4;
+    for (uint32_t b0 = warp * 32; b0 < count; b0 += kBatch * nwarps * 32) {
+        uint64_t hv[kBatch], hn[kBatch], hp[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const uint32_t base = b0 + (uint32_t)j * nwarps * 32;
+            const uint64_t i = start + base + lane;
+            const bool ok = base + lane < count;
+            hv[j] = ok ? hi[i] : 0;
+            hn[j] = (ok && i + 1 < seg_end) ? hi[i + 1] : 0;
+            hp[j] = (ok && lane == 0 && i > si.start) ? hi[i - 1] : 0;
         }
-        uint32_t starts = __ballot_sync(0xffffffffu, run_start);
-        while (starts) {
-            const int src = __ffs(starts) - 1;
-            starts &= starts - 1;
-            const uint64_t rs = start + base + src;
-            const uint64_t key = hi[rs] >> run_shift;
-            const uint64_t e = rs + lane;
-            const bool in = e < seg_end && (hi[e] >> run_shift) == key;
-            const uint32_t inmask = __ballot_sync(0xffffffffu, in);
-            const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
-            if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == key) {
-                if (lane == 0) atomicOr(long_run, 1u);
-                continue;
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const uint32_t base = b0 + (uint32_t)j * nwarps * 32;
+            const uint64_t i = start + base + lane;
+            const bool ok = base + lane < count;
+            const uint64_t key = hv[j] >> run_shift;
+            // every lane takes part in the shuffle; lane 0 then uses its own load
+            const uint64_t up = __shfl_up_sync(0xffffffffu, hv[j], 1);
+            const uint64_t prev = lane == 0 ? hp[j] : up;
+            const bool run_start = ok && i + 1 < seg_end && (hn[j] >> run_shift) == key &&
+                                   !(i > si.start && (prev >> run_shift) == key);
+            uint32_t starts = __ballot_sync(0xffffffffu, run_start);
+            while (starts) {
+                const int src = __ffs(starts) - 1;
+                starts &= starts - 1;
+                const uint64_t rs = start + base + src;
+                const uint64_t rkey = hi[rs] >> run_shift;
+                const uint64_t e = rs + lane;
+                const bool in = e < seg_end && (hi[e] >> run_shift) == rkey;
+                const uint32_t inmask = __ballot_sync(0xffffffffu, in);
+                const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
+                if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == rkey) {
+                    if (lane == 0) atomicOr(long_run, 1u);
+                    continue;
+                }
+                const bool mine = (uint32_t)lane < len;
+                const uint64_t h = mine ? hi[e] : ~0ull;
+                const uint32_t d = mine ? ids[e] : 0xFFFFFFFFu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, h);
+                const uint64_t l = (mine && __popc(peers) > 1)
+                                       ? row_key_lo(rows.db, rows.row_bytes, rows.P, d, curve)
+                                       : 0;
+                uint32_t rank = 0;
+                for (uint32_t u = 0; u < len; ++u) {
+                    const uint64_t hu = __shfl_sync(0xffffffffu, h, (int)u);
+                    const uint64_t lu = __shfl_sync(0xffffffffu, l, (int)u);
+                    const uint32_t du = __shfl_sync(0xffffffffu, d, (int)u);
+                    rank += (hu < h || (hu == h && (lu < l || (lu == l && du < d)))) ? 1u : 0u;
+                }
+                __syncwarp();
+                if (mine) {
+                    hi[rs + rank] = h;
+                    ids[rs + rank] = d;
+                }
+                __syncwarp();
             }
-            const bool mine = (uint32_t)lane < len;
-            const uint64_t h = mine ? hi[e] : ~0ull;
-            const uint32_t d = mine ? ids[e] : 0xFFFFFFFFu;
-            const uint32_t peers = __match_any_sync(0xffffffffu, h);
-            const uint64_t l = (mine && __popc(peers) > 1)
-                                   ? row_key_lo(rows.db, rows.row_bytes, rows.P, d, curve)
-                                   : 0;
-            uint32_t rank = 0;
-            for (uint32_t u = 0; u < len; ++u) {
-                const uint64_t hu = __shfl_sync(0xffffffffu, h, (int)u);
-                const uint64_t lu = __shfl_sync(0xffffffffu, l, (int)u);
-                const uint32_t du = __shfl_sync(0xffffffffu, d, (int)u);
-                rank += (hu < h || (hu == h && (lu < l || (lu == l && du < d)))) ? 1u : 0u;
-            }
-            __syncwarp();
-            if (mine) {
-                hi[rs + rank] = h;
-                ids[rs + rank] = d;
-            }
-            __syncwarp();
         }
     }
 }
