@@ -438,9 +438,13 @@ __global__ void __launch_bounds__(256) fixup_runs_kernel(uint64_t* hi, uint32_t*
                 const int src = __ffs(starts) - 1;
                 starts &= starts - 1;
                 const uint64_t rs = start + base + src;
-                const uint64_t rkey = hi[rs] >> run_shift;
+                const uint64_t rkey = __shfl_sync(0xffffffffu, key, src);
+                // the run's records, one per lane, words and ids loaded together
                 const uint64_t e = rs + lane;
-                const bool in = e < seg_end && (hi[e] >> run_shift) == rkey;
+                const bool inseg = e < seg_end;
+                const uint64_t he = inseg ? hi[e] : ~0ull;
+                const uint32_t de = inseg ? ids[e] : 0xFFFFFFFFu;
+                const bool in = inseg && (he >> run_shift) == rkey;
                 const uint32_t inmask = __ballot_sync(0xffffffffu, in);
                 const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
                 if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == rkey) {
@@ -448,8 +452,8 @@ __global__ void __launch_bounds__(256) fixup_runs_kernel(uint64_t* hi, uint32_t*
                     continue;
                 }
                 const bool mine = (uint32_t)lane < len;
-                const uint64_t h = mine ? hi[e] : ~0ull;
-                const uint32_t d = mine ? ids[e] : 0xFFFFFFFFu;
+                const uint64_t h = mine ? he : ~0ull;
+                const uint32_t d = mine ? de : 0xFFFFFFFFu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, h);
                 const uint64_t l = (mine && __popc(peers) > 1)
                                        ? row_key_lo(rows.db, rows.row_bytes, rows.P, d, curve)
