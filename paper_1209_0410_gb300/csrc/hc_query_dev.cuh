@@ -137,19 +137,6 @@ __device__ __forceinline__ void chunk_candidates_n(const uint8_t* __restrict__ d
     }
 }
 
-// The single-candidate form (LPR <= 8): lane l holds row
-// (l % LPR) * (32 / LPR) + l / LPR of the chunk.
-template <bool F32, int LPR>
-__device__ __forceinline__ uint64_t chunk_candidates(const uint8_t* __restrict__ db,
-                                                     uint32_t row_bytes, const uint8_t* qrow,
-                                                     uint4 qv0, uint32_t id, uint32_t cnt,
-                                                     int lane) {
-    static_assert(ChunkWidth<LPR>::NG == 1, "wider rows give several candidates per lane");
-    uint64_t out[1];
-    chunk_candidates_n<F32, LPR>(db, row_bytes, qrow, qv0, id, cnt, lane, out);
-    return out[0];
-}
-
 // Low key word of entry g (global entry index) of list L.
 __device__ __forceinline__ uint64_t entry_key_lo(const IndexView& ix, uint32_t L, uint64_t g) {
     if (ix.keys_lo) return __ldg(ix.keys_lo + g);
