@@ -298,6 +298,42 @@ def test_build_long_runs_of_equal_keys(hc, parts, copies):
     idx.free()
 
 
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 70])
+def test_query_tiny_databases(hc, n):
+    """Lists shorter than one 32-entry step: the packed walk fills steps from
+    several windows and pads the top-k when fewer than k rows exist."""
+    db, q = make_case(n, 40, seed=n + 11)
+    idx = hc.hc_build(dev(db))
+    oidx = O.build(db, curves=8, m=16)
+    for k, p in [(10, 2), (10, 100), (1, 1), (128, 40)]:
+        ids, dist = hc.hc_query(idx, dev(q), k, p)
+        sync()
+        rids, rdist = O.search(oidx, db, q, k, p)
+        assert np.array_equal(ids.cpu().numpy(), rids)
+        assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+    idx.free()
+
+
+def test_query_depths_per_query_matches_fixed(hc):
+    """hc_query_depths with a different depth per query (0 included) equals
+    one fixed-depth query per distinct depth."""
+    import torch
+    n, nq = 15013, 257
+    db, q = make_case(n, nq, seed=41)
+    idx = hc.hc_build(dev(db))
+    rng = np.random.default_rng(3)
+    depths = rng.choice([0, 1, 5, 16, 31, 32, 33, 100, 700], size=nq).astype(np.int32)
+    ids, dist = hc.hc_query_depths(idx, dev(q), 10, torch.from_numpy(depths).cuda())
+    sync()
+    oidx = O.build(db, curves=8, m=16)
+    for p in np.unique(depths):
+        sel = np.flatnonzero(depths == p)
+        rids, rdist = O.search(oidx, db, q[sel], 10, int(p))
+        assert np.array_equal(ids.cpu().numpy()[sel], rids)
+        assert np.array_equal(dist.cpu().numpy()[sel], O.int32_dist(rdist))
+    idx.free()
+
+
 @pytest.mark.parametrize("nq", [0, 1, 7, 9, 1000])
 def test_query_batch_sizes(hc, nq):
     n = 6000
