@@ -4,17 +4,19 @@
 //
 // One warp per query:
 //   K1  lanes c < curves compute the query's extended-key on curve c;
-//   K3  lanes L < lists run lower_bound in list L (128-bit compares, the low
-//       word is read only when the high words tie);
-//   K4  for every list, the window [max(0,pos-p), min(n,pos+p)) is walked 32
-//       entries at a time: the 32 ids are one coalesced load, then each row
-//       is read as 16-byte vectors by LPR lanes (LPR = 8 for 128-byte uint8
-//       rows: four rows per warp instruction).  Rows of at most 128 bytes are
-//       staged: the next step's rows are copied into a two-step per-warp
-//       shared-memory ring with cp.async while the current step is reduced,
-//       across window ends, so the bytes in flight are bounded by shared
-//       memory instead of registers; wider rows are gathered into registers,
-//       eight 16-byte loads in flight per lane.  uint8 partial distances use
+//   K3  lanes L < lists run lower_bound in list L (128-bit compares; the low
+//       word is consulted only when the high words tie, recomputed from the
+//       entry's row when the index keeps high words only);
+//   K4  the windows [max(0,pos-p), min(n,pos+p)) are walked 32 entries at a
+//       time: the 32 ids are one load, then each row is read as 16-byte
+//       vectors by LPR lanes (LPR = 8 for 128-byte uint8 rows: four rows per
+//       warp instruction).  Rows of at most 128 bytes are staged: all windows
+//       of the query are packed back to back (a step may span several), and
+//       the next step's rows are copied into a two-step per-warp shared-
+//       memory ring with cp.async while the current step is reduced, so the
+//       bytes in flight are bounded by shared memory instead of registers;
+//       wider rows are gathered into registers, eight 16-byte loads in flight
+//       per lane.  uint8 partial distances use
 //       vabsdiffu4 + dp4a (exact in 32-bit integers), float32 use fma;
 //       a reduce-scatter over the LPR lanes leaves lane l with the distance
 //       of one row of the 32 (LPR-1 shuffles for LPR partial sums);

@@ -10,6 +10,13 @@
 //   - at the end the low words and ids are gathered by the final positions.
 // Digits above key_bits are zero by contract and are skipped.
 //
+// When the caller may wait once on the stream (hc_build), the high-word-first
+// path sorts only the top bytes of the high word (hi_skip low bytes left out)
+// and a fix-up orders the short runs of equal prefixes by (high word, low
+// word, id).  For an index with affine ids and no stored low words the last
+// pass writes the final high words and ids and the fix-up works in place;
+// a run longer than 32 sends the caller back for a sort by every byte.
+//
 // Per pass, three kernels, none of which waits on another block:
 //   hist    one 4096-record tile per block: digit counts -> counts[seg][digit][tile]
 //   scan    one block per (segment, digit): exclusive scan over the tiles
