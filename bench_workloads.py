@@ -95,6 +95,14 @@ def run_uneven(a):
     launches = (hc.hc_launch_count() - launches0) // reps
     persistent_ms = e0.elapsed_time(e1) / reps
     same = all(torch.equal(j.ids, r[0]) for j, r in zip(jobs, ref))
+    # the method's own bytes for all jobs (window rows and ids, probes, queries, results)
+    from bench import algorithmic_query_bytes, measured_peaks
+    qbytes = 0
+    for sh, j in zip(shapes, jobs):
+        row_bytes = sh["d"] * (4 if sh["dtype"] == "f32" else 1)
+        if sh["nq"]:
+            qbytes += algorithmic_query_bytes(hc, j.index, j.q, j.p, j.k, row_bytes)[0]
+    peak_gbs = measured_peaks()[0]["hbm_gbs"]
     _line({"metric": "queries/s, 64 uneven indexes in one persistent launch (CUDA graph)",
            "value": total_q / (persistent_ms / 1e3), "unit": "queries/s", "n_gpus": 1,
            "steps": reps, "warmup": a.warmup, "ms_per_step": persistent_ms,
@@ -110,7 +118,10 @@ def run_uneven(a):
                       "speedup_vs_per_index": per_index_ms / persistent_ms,
                       "autotuned_config": cfg, "tune_s": tune_s, "setup_s": setup_s,
                       "results_identical_to_per_index": same,
-                      "kernel_launches_per_step": launches}})
+                      "kernel_launches_per_step": launches,
+                      "algorithmic_bytes": qbytes,
+                      "hbm_frac_persistent": qbytes / (persistent_ms / 1e3) / 1e9 / peak_gbs,
+                      "hbm_frac_per_index": qbytes / (per_index_ms / 1e3) / 1e9 / peak_gbs}})
     plan.free()
     return 0
 
