@@ -109,7 +109,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     return before + x - v;
 }
 
+// digits (null: read the words): this pass's digit of every record, one byte
+// each, written by the previous pass's scatter
 __global__ void __launch_bounds__(kThreads) hist_kernel(const uint64_t* __restrict__ words,
+                                                        const uint8_t* __restrict__ digits,
                                                         int shift, uint32_t nseg,
                                                         const SegInfo* __restrict__ segs,
                                                         uint32_t* __restrict__ counts) {
@@ -120,10 +123,16 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const uint64_t* __restri
     tile_of(nseg, segs, si, seg, lt, start, count);
     h[threadIdx.x] = 0;
     __syncthreads();
-    const uint64_t* w = words + start;
+    if (digits) {
+        const uint8_t* dg = digits + start;
 #pragma unroll 4
-    for (uint32_t i = threadIdx.x; i < count; i += kThreads)
-        atomicAdd(&h[(uint32_t)(__ldg(w + i) >> shift) & 0xFFu], 1u);
+        for (uint32_t i = threadIdx.x; i < count; i += kThreads) atomicAdd(&h[__ldg(dg + i)], 1u);
+    } else {
+        const uint64_t* w = words + start;
+#pragma unroll 4
+        for (uint32_t i = threadIdx.x; i < count; i += kThreads)
+            atomicAdd(&h[(uint32_t)(__ldg(w + i) >> shift) & 0xFFu], 1u);
+    }
     __syncthreads();
     counts[si.cnt_base + (uint64_t)threadIdx.x * si.ntiles + lt] = h[threadIdx.x];
 }
@@ -189,11 +198,14 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
 // in record order.  Records past the tile's end carry digit 255 and sort last.
 // id_base (final pass of an affine-id sort, else null): the carried
 // positions leave as ids, id = id_base[seg] + position - segment start.
+// next_digit (null: none): the next pass's digit of every record, one byte
+// each at its destination, so the next histogram reads bytes, not words.
 __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
     const uint64_t* __restrict__ wsrc, const uint32_t* __restrict__ psrc,
     uint64_t* __restrict__ wdst, uint32_t* __restrict__ pdst, int shift, uint32_t nseg,
     const SegInfo* __restrict__ segs, const uint32_t* __restrict__ counts,
-    const uint32_t* __restrict__ totals, const uint64_t* __restrict__ id_base) {
+    const uint32_t* __restrict__ totals, const uint64_t* __restrict__ id_base,
+    uint8_t* __restrict__ next_digit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem& sm = *reinterpret_cast<ScatterSmem*>(smem_raw);
 
@@ -274,6 +286,7 @@ __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
         const uint64_t g = sm.gbase[(uint32_t)(v >> shift) & 0xFFu] + i;
         wdst[g] = v;
         pdst[g] = sm.p[padp(i)] + idoff;
+        if (next_digit) next_digit[g] = (uint8_t)(v >> (shift + 8));
     }
 }
 
@@ -492,7 +505,7 @@ struct Layout {
     uint32_t nseg = 0, ntiles = 0;
     uint64_t ncounts = 0;
     size_t off_w = 0, off_pa = 0, off_pb = 0, off_counts = 0, off_totals = 0, off_segs = 0,
-           off_flag = 0, bytes = 0;
+           off_flag = 0, off_digits = 0, bytes = 0;
 };
 
 Layout make_layout(const SortProblem& p) {
@@ -513,6 +526,7 @@ Layout make_layout(const SortProblem& p) {
     L.off_totals = o;  o = align_up(o + sizeof(uint32_t) * 256 * (L.nseg ? L.nseg : 1));
     L.off_segs = o;    o = align_up(o + sizeof(SegInfo) * (L.nseg ? L.nseg : 1));
     L.off_flag = o;    o = align_up(o + sizeof(uint32_t));
+    L.off_digits = o;  o = align_up(o + L.total);
     L.bytes = o;
     return L;
 }
@@ -587,6 +601,9 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     const int hi_passes = std::max(digits - 8, 0);
     const dim3 scan_grid(256, L.nseg);
     uint32_t* flag = reinterpret_cast<uint32_t*>(base + L.off_flag);
+    // next-pass digits, one byte per record, written by a scatter for the
+    // following histogram (within one key word)
+    uint8_t* dgt = reinterpret_cast<uint8_t*>(base + L.off_digits);
 
     if (p.allow_sync && hi_passes > 0 && L.ntiles) {
         // sort by the high word's top bytes alone (skipping its lowest
@@ -606,11 +623,13 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             const int shift = (t & 7) * 8;
             const bool last = t + 1 == 8 + hi_passes;
             uint32_t* pd = (last && in_place) ? p.out_ids : pbuf_of(pa, pb, pn);
-            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cw, shift, L.nseg, segs, counts);
+            const bool first = t == 8 + skip;
+            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cw, first ? nullptr : dgt, shift, L.nseg,
+                                                      segs, counts);
             scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
             scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(
                 cw, cp, wb[wn], pd, shift, L.nseg, segs, counts, totals,
-                (last && in_place) ? p.id_base_dev : nullptr);
+                (last && in_place) ? p.id_base_dev : nullptr, last ? nullptr : dgt);
             count_launches(3);
             if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
             cw = wb[wn];
@@ -652,16 +671,20 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
 
     const uint64_t* cur_w = p.lo;
     const uint32_t* cur_p = nullptr;
-    auto run_pass = [&](int digit) -> int {
+    // digits of the next pass were written by the previous scatter when both
+    // passes read the same key word
+    bool have_digits = false;
+    auto run_pass = [&](int digit, bool next_same_word) -> int {
         const int shift = (digit & 7) * 8;
         if (L.ntiles) {
-            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cur_w, shift, L.nseg, segs, counts);
+            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cur_w, have_digits ? dgt : nullptr, shift,
+                                                      L.nseg, segs, counts);
             scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
             uint64_t* wd = wbuf[wnext];
             uint32_t* pd = pbuf[pnext];
-            scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(cur_w, cur_p, wd, pd, shift,
-                                                                L.nseg, segs, counts, totals,
-                                                                nullptr);
+            scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(
+                cur_w, cur_p, wd, pd, shift, L.nseg, segs, counts, totals, nullptr,
+                next_same_word ? dgt : nullptr);
             count_launches(3);
             if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
             cur_w = wd;
@@ -669,10 +692,11 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             wnext ^= 1;
             pnext ^= 1;
         }
+        have_digits = next_same_word;
         return HC_OK;
     };
     for (int t = 0; t < lo_passes; ++t)
-        if (int rc = run_pass(t)) return rc;
+        if (int rc = run_pass(t, t + 1 < lo_passes && (t & 7) != 7)) return rc;
     {
         uint64_t* wd = wbuf[wnext];
         gather_words_kernel<<<grid_stride_blocks(L.total), 256, 0, s>>>(p.hi, cur_p, wd, L.total);
@@ -681,8 +705,9 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
         cur_w = wd;
         wnext ^= 1;
     }
+    have_digits = false;   // the high words were just gathered
     for (int t = 8; t < 8 + hi_passes; ++t)
-        if (int rc = run_pass(t)) return rc;
+        if (int rc = run_pass(t, t + 1 < 8 + hi_passes && (t & 7) != 7)) return rc;
     if (cur_w != p.out_hi) return HC_ERR_STATE;  // buffer bookkeeping broken
     gather_final_kernel<<<L.ntiles, 256, 0, s>>>(p.lo, FinalIds{p.ids, p.id_base_dev}, cur_p,
                                                   p.out_lo, p.out_ids, L.nseg, segs);
