@@ -1,9 +1,9 @@
 // K1: Hilbert extended-keys of database rows (Algorithm 1, per-curve step)
 // and of standalone vectors.  One thread per row computes the keys of every
-// curve; the Hilbert map itself is ALU work (about 800 integer operations
-// per 16-coordinate key), the row read and the 20 bytes written per key are
-// coalesced across the warp (the low words are written only when the index
-// keeps them).
+// curve, four 16-coordinate keys at a time as byte lanes of 32-bit words;
+// the Hilbert map itself is ALU work, and for an index that keeps high words
+// only, just the levels that decide bit planes 7..4 are run.  The row read
+// and the key words written are coalesced across the warp.
 #include "hc_internal.h"
 
 namespace hc {
