@@ -70,6 +70,9 @@ def parse_args():
     ap.add_argument("--dtype", choices=["u8", "f32"], default="u8")
     ap.add_argument("--sweep", default="32,128,512", help="query-only p sweep ('' = none)")
     ap.add_argument("--recall-sample", type=int, default=2000)
+    ap.add_argument("--input-order", action="store_true",
+                    help="answer the queries in input order (hc_query) instead of curve-0 key "
+                         "order (hc_query_ordered)")
     ap.add_argument("--quick", action="store_true",
                     help="timed steps only: no sweep, recall, e2e or CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -325,11 +328,21 @@ def run_hc(a):
         if world > 1:
             dist.barrier()
 
+    workspace = torch.empty(hc.hc_query_ordered_workspace(a.nq), dtype=torch.uint8,
+                            device="cuda")
+
+    def query(idx, p=None):
+        if a.input_order:
+            hc.hc_query(idx, q, a.k, a.p if p is None else p, out_ids, out_dist, stream=stream)
+        else:
+            hc.hc_query_ordered(idx, q, a.k, a.p if p is None else p, out_ids, out_dist,
+                                workspace=workspace, stream=stream)
+
     def step(ev):
         ev[0].record(stream)
         idx = hc.hc_build(db, 8, 16, stream=stream)
         ev[1].record(stream)
-        hc.hc_query(idx, q, a.k, a.p, out_ids, out_dist, stream=stream)
+        query(idx)
         ev[2].record(stream)
         idx.free()
 
@@ -377,7 +390,8 @@ def run_hc(a):
     achieved = qbytes / (q_ms / 1000.0) / 1e9
     # the committed capture is of the default workload only
     traffic, _ = ncu_traffic("query_kernel")
-    if (a.n_db, a.nq, a.p, a.k, a.dtype) != (10_000_000, 100_000, 128, 10, "u8"):
+    if (a.n_db, a.nq, a.p, a.k, a.dtype, a.input_order) != (10_000_000, 100_000, 128, 10, "u8",
+                                                            False):
         traffic = None
     roofline = {"kernel": "query_kernel (fused K1+K3+K4+K5+K6)", "bound": "hbm",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -389,6 +403,8 @@ def run_hc(a):
 
     cfg = {"workload": workload_name(a), "n_db": a.n_db, "nq": a.nq, "p": a.p, "k": a.k,
            "curves": 8, "dims_per_curve": 16, "partitions": 1,
+           "query_order": ("input order (hc_query)" if a.input_order else
+                           "curve-0 key order (hc_query_ordered; results identical)"),
            "l2": "inputs larger than L2 (database %.2f GB, index %.2f GB vs 129 MB L2)"
                  % (a.n_db * row_bytes / 1e9, a.n_db * 8 * 12 / 1e9),
            "build_ms": statistics.mean(build_ms), "query_ms": q_ms,
@@ -406,11 +422,11 @@ def run_hc(a):
         sweep = []
         for p in [int(x) for x in a.sweep.split(",") if x.strip()]:
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            hc.hc_query(idx, q, a.k, p, out_ids, out_dist, stream=stream)
+            query(idx, p)
             ev[0].record(stream)
             reps = 3
             for _ in range(reps):
-                hc.hc_query(idx, q, a.k, p, out_ids, out_dist, stream=stream)
+                query(idx, p)
             ev[1].record(stream)
             torch.cuda.synchronize()
             ms = ev[0].elapsed_time(ev[1]) / reps

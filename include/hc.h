@@ -135,6 +135,24 @@ HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, u
                     int32_t* out_ids_dev, void* out_dist_dev, void* cuda_stream);
 
 /*
+ * hc_query_ordered -- hc_query with the queries answered in the order of
+ * their curve-0 extended-keys (the top 32 key bits, radix-sorted on the
+ * device), so that queries answered at the same time read overlapping
+ * windows and share their rows in L2.  The paper batches queries in arrival
+ * order (Sec. 5.1); the order changes no result: every query's ids and
+ * distances land in its own row and equal those of hc_query.
+ *   workspace_dev    device memory of at least hc_query_ordered_workspace(nq)
+ *                    bytes, 256-byte aligned, owned by the caller (contents
+ *                    scratch; one call at a time per workspace)
+ * Other arguments as hc_query.  No allocation; asynchronous on cuda_stream.
+ * HC_ERR_ARG if the workspace is missing, misaligned or too small.
+ */
+HC_API size_t hc_query_ordered_workspace(uint32_t nq);
+HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
+                            int32_t* out_ids_dev, void* out_dist_dev, void* workspace_dev,
+                            size_t workspace_bytes, void* cuda_stream);
+
+/*
  * hc_query_host -- hc_query from HOST buffers: copies the queries in, runs
  * the query kernel and copies the results back, on cuda_stream, and returns
  * once the results are in the host buffers.  Device staging buffers are

@@ -344,6 +344,81 @@ HC_API int hc_query_at(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k
                                   static_cast<cudaStream_t>(cuda_stream), nullptr, pos_dev));
 }
 
+}  // extern "C"
+
+namespace {
+
+// Workspace of hc_query_ordered for nq queries: sort keys, the segment table,
+// the sorted keys and the permutation, then the sort's own scratch.
+struct OrderLayout {
+    size_t keys = 0, seg = 0, out_hi = 0, out_lo = 0, order = 0, sort = 0, bytes = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+SortProblem order_problem(uint32_t nq) {
+    SortProblem sp;
+    sp.seg_off = {0, (uint64_t)nq};
+    sp.key_bits = 32;
+    sp.allow_sync = false;   // no stream wait: every key byte is sorted
+    return sp;
+}
+
+OrderLayout order_layout(uint32_t nq) {
+    OrderLayout L;
+    size_t o = 0;
+    L.keys = o;    o = align256(o + 8ull * nq);
+    L.seg = o;     o = align256(o + 8 * 3);      // seg_off[2], id_base[1]
+    L.out_hi = o;  o = align256(o + 8ull * nq);
+    L.out_lo = o;  o = align256(o + 8ull * nq);
+    L.order = o;   o = align256(o + 4ull * nq);
+    L.sort = o;    o = align256(o + sort_scratch_bytes(order_problem(nq)));
+    L.bytes = o;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+HC_API size_t hc_query_ordered_workspace(uint32_t nq) { return nq ? order_layout(nq).bytes : 0; }
+
+HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
+                            int32_t* out_ids_dev, void* out_dist_dev, void* workspace_dev,
+                            size_t workspace_bytes, void* cuda_stream) {
+    if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
+    if (nq == 0) return HC_OK;
+    if (!q_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev) || !workspace_dev ||
+        ((uintptr_t)workspace_dev & 255))
+        return HC_ERR_ARG;
+    const OrderLayout L = order_layout(nq);
+    if (workspace_bytes < L.bytes) return HC_ERR_ARG;
+    if (!is_device_ptr(q_dev) || !is_device_ptr(out_ids_dev) || !is_device_ptr(out_dist_dev) ||
+        !is_device_ptr(workspace_dev))
+        return HC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    char* ws = static_cast<char*>(workspace_dev);
+    uint64_t* keys = reinterpret_cast<uint64_t*>(ws + L.keys);
+    uint64_t* seg = reinterpret_cast<uint64_t*>(ws + L.seg);
+    const IndexView v = view_of(idx);
+    int rc = status_of(launch_order_keys(v, q_dev, nq, keys, s));
+    const uint64_t small[3] = {0, (uint64_t)nq, 0};   // seg_off, then id_base
+    if (!rc) rc = status_of(upload_small(seg, small, sizeof(small), s));
+    if (rc) return rc;
+    SortProblem sp = order_problem(nq);
+    sp.seg_off_dev = seg;
+    sp.hi = keys;   // gathered along, not compared (key_bits = 32)
+    sp.lo = keys;
+    sp.ids = nullptr;
+    sp.id_base_dev = seg + 2;   // ids = positions 0..nq-1
+    sp.out_hi = reinterpret_cast<uint64_t*>(ws + L.out_hi);
+    sp.out_lo = reinterpret_cast<uint64_t*>(ws + L.out_lo);
+    sp.out_ids = reinterpret_cast<uint32_t*>(ws + L.order);
+    if ((rc = sort_segments(sp, ws + L.sort, s))) return rc;
+    return status_of(launch_query(v, q_dev, nq, k, p, out_ids_dev, out_dist_dev, s, nullptr,
+                                  nullptr, sp.out_ids));
+}
+
 HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids_host, void* out_dist_host, void* cuda_stream) {
     if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;

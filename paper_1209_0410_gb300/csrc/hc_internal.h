@@ -105,9 +105,16 @@ struct IndexView {
 // earlier (hc_query_positions), so the kernel skips its own search.
 // Low key words of every entry (list_off order) of an index without keys_lo.
 cudaError_t launch_entry_lo(const IndexView& ix, uint64_t* out, cudaStream_t s);
+// order (device, nq entries, nullable): warp w answers query order[w] (a
+// permutation of 0..nq-1); results still land at each query's own row.
 cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids, void* out_dist, cudaStream_t s,
-                         const uint32_t* p_query = nullptr, const int64_t* pos_in = nullptr);
+                         const uint32_t* p_query = nullptr, const int64_t* pos_in = nullptr,
+                         const uint32_t* order = nullptr);
+// The top 32 bits of each query's curve-0 extended-key, as the low word of a
+// sort key (the order in which hc_query_ordered answers the queries).
+cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, uint64_t* keys,
+                              cudaStream_t s);
 cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, int64_t* pos,
                              cudaStream_t s);
 cudaError_t launch_bruteforce(const void* db, hc_dtype dtype, uint64_t n, uint32_t d,

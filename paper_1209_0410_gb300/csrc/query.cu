@@ -46,6 +46,7 @@ struct QueryArgs {
     int64_t* out_pos;            // positions-only kernel
     const uint32_t* p_query;     // per-query depth (overrides p), or null
     const int64_t* pos_in;       // precomputed lower_bound positions (nq x lists), or null
+    const uint32_t* order;       // warp w answers query order[w], or null (w itself)
 };
 
 #ifndef HC_QUERY_MIN_BLOCKS
@@ -60,8 +61,9 @@ template <bool F32, int LPR, int KR, bool STAGED>
 __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kernel(QueryArgs a) {
     extern __shared__ __align__(16) uint32_t s_pos[];  // kQWarps x lists, then the rings
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t qi = blockIdx.x * kQWarps + warp;
-    if (qi >= a.nq) return;
+    const uint32_t w = blockIdx.x * kQWarps + warp;
+    if (w >= a.nq) return;
+    const uint32_t qi = a.order ? __ldg(a.order + w) : w;
     const IndexView& ix = a.ix;
     const uint8_t* qrow = static_cast<const uint8_t*>(a.q) + (size_t)qi * ix.row_bytes;
     const uint32_t depth = a.p_query ? __ldg(a.p_query + qi) : a.p;
@@ -81,6 +83,19 @@ __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kerne
     }
     top.template store<F32>(a.k, lane, a.out_ids + (size_t)qi * a.k,
                             static_cast<uint32_t*>(a.out_dist) + (size_t)qi * a.k);
+}
+
+// keys[i] = top 32 bits of query i's curve-0 extended-key (one thread each)
+__global__ void __launch_bounds__(256) order_keys_kernel(IndexView ix, const uint8_t* q,
+                                                         uint32_t nq, uint64_t* keys) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    uint64_t h, l;
+    curve_key_call(q + (size_t)i * ix.row_bytes, ix.P, 0, h, l);
+    const uint32_t bits = 8 * ix.P.m;   // key bits, right-aligned in (h, l)
+    const uint64_t top = bits > 64 ? (h << (128 - bits)) | (bits < 128 ? l >> (bits - 64) : 0)
+                                   : l << (64 - bits);
+    keys[i] = top >> 32;
 }
 
 __global__ void __launch_bounds__(kQWarps * 32) positions_kernel(QueryArgs a) {
@@ -126,17 +141,27 @@ struct QueryLaunch {
 
 cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids, void* out_dist, cudaStream_t s,
-                         const uint32_t* p_query, const int64_t* pos_in) {
+                         const uint32_t* p_query, const int64_t* pos_in,
+                         const uint32_t* order) {
     if (nq == 0) return cudaSuccess;
-    QueryArgs a{ix, q, nq, k, p, out_ids, out_dist, nullptr, p_query, pos_in};
+    QueryArgs a{ix, q, nq, k, p, out_ids, out_dist, nullptr, p_query, pos_in, order};
     return dispatch<QueryLaunch>(ix.P.dtype == HC_F32, lanes_per_row(ix.row_bytes), regs_for_k(k),
                                  a, s);
+}
+
+cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, uint64_t* keys,
+                              cudaStream_t s) {
+    if (nq == 0) return cudaSuccess;
+    order_keys_kernel<<<(nq + 255) / 256, 256, 0, s>>>(ix, static_cast<const uint8_t*>(q), nq,
+                                                       keys);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, int64_t* pos,
                              cudaStream_t s) {
     if (nq == 0) return cudaSuccess;
-    QueryArgs a{ix, q, nq, 1, 0, nullptr, nullptr, pos, nullptr, nullptr};
+    QueryArgs a{ix, q, nq, 1, 0, nullptr, nullptr, pos, nullptr, nullptr, nullptr};
     const unsigned blocks = (nq + kQWarps - 1) / kQWarps;
     positions_kernel<<<blocks, kQWarps * 32, sizeof(uint32_t) * kQWarps * ix.lists, s>>>(a);
     count_launches(1);

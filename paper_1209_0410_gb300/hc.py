@@ -94,6 +94,10 @@ def lib():
         L.hc_bruteforce.argtypes = [_vp, ctypes.c_int, _u64, _u32, _vp, _u32, _u32, _vp, _vp, _vp]
         L.hc_query_depths.argtypes = [_vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]
         L.hc_query_at.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp, _vp]
+        L.hc_query_ordered_workspace.restype = ctypes.c_size_t
+        L.hc_query_ordered_workspace.argtypes = [_u32]
+        L.hc_query_ordered.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp,
+                                       ctypes.c_size_t, _vp]
         L.hc_serve_create_ex.argtypes = [ctypes.POINTER(_vp), _u32, _u64,
                                          ctypes.POINTER(_ServeParams), ctypes.POINTER(_vp)]
         L.hc_serve_create.argtypes = [ctypes.POINTER(_vp), _u32, _u64, ctypes.POINTER(_vp)]
@@ -262,6 +266,31 @@ def hc_query_at(index, q, k, p, positions, out_ids=None, out_dist=None, stream=N
         _check(lib().hc_query_at(index.handle, _dev(q, "q"), nq, k, p, _dev(positions, "pos"),
                                  _dev(out_ids, "out_ids"), _dev(out_dist, "out_dist"),
                                  _stream(stream)), "hc_query_at")
+    return out_ids, out_dist
+
+
+def hc_query_ordered_workspace(nq):
+    """Bytes of device workspace hc_query_ordered needs for nq queries."""
+    return int(lib().hc_query_ordered_workspace(nq))
+
+
+def hc_query_ordered(index, q, k, p, out_ids=None, out_dist=None, workspace=None, stream=None):
+    """hc_query answering the queries in curve-0 key order (results identical);
+    workspace: a CUDA uint8 tensor of at least hc_query_ordered_workspace(nq)
+    bytes (allocated here when None)."""
+    nq = q.shape[0]
+    if out_ids is None:
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+    if out_dist is None:
+        out_dist = torch.empty((nq, k), dtype=_dist_dtype(index.dtype), device=q.device)
+    if nq:
+        need = hc_query_ordered_workspace(nq)
+        if workspace is None:
+            workspace = torch.empty(need, dtype=torch.uint8, device=q.device)
+        _check(lib().hc_query_ordered(index.handle, _dev(q, "q"), nq, k, p,
+                                      _dev(out_ids, "out_ids"), _dev(out_dist, "out_dist"),
+                                      _dev(workspace, "workspace"), workspace.numel(),
+                                      _stream(stream)), "hc_query_ordered")
     return out_ids, out_dist
 
 

@@ -28,7 +28,7 @@ def test_header_declares_entry_points():
     syms = declared_symbols()
     for name in ("hc_build", "hc_query", "hc_free", "hc_strerror", "hc_query_host",
                  "hc_build_host", "hc_hilbert_keys", "hc_sort_keys", "hc_query_positions",
-                 "hc_bruteforce"):
+                 "hc_bruteforce", "hc_query_ordered", "hc_query_ordered_workspace"):
         assert name in syms
 
 

@@ -334,6 +334,36 @@ def test_query_depths_per_query_matches_fixed(hc):
     idx.free()
 
 
+@pytest.mark.parametrize("dtype,nq,k,p,parts", [("u8", 1000, 10, 64, 1), ("u8", 1, 10, 50, 1),
+                                                 ("u8", 7, 33, 20, 1), ("u8", 2049, 100, 30, 3),
+                                                 ("f32", 300, 10, 40, 1)])
+def test_query_ordered_equals_query(hc, dtype, nq, k, p, parts):
+    """Answering the queries in curve-0 key order changes no result."""
+    import torch
+    db, q = make_case(20011, nq, seed=nq + 5, dtype=dtype)
+    idx = hc.hc_build(dev(db), partitions=parts)
+    ids_a, dist_a = hc.hc_query(idx, dev(q), k, p)
+    ids_b, dist_b = hc.hc_query_ordered(idx, dev(q), k, p)
+    sync()
+    assert torch.equal(ids_a, ids_b)
+    assert torch.equal(dist_a.view(torch.int32), dist_b.view(torch.int32))
+    if dtype == "u8":
+        oidx = O.build(db, curves=8, m=16, ell=parts)
+        rids, _ = O.search(oidx, db, q, k, p)
+        assert np.array_equal(ids_b.cpu().numpy(), rids)
+    idx.free()
+
+
+def test_query_ordered_rejects_a_small_workspace(hc):
+    import torch
+    db, q = make_case(5000, 100, seed=2)
+    idx = hc.hc_build(dev(db))
+    ws = torch.empty(hc.hc_query_ordered_workspace(100) - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(hc.HCError):
+        hc.hc_query_ordered(idx, dev(q), 10, 20, workspace=ws)
+    idx.free()
+
+
 @pytest.mark.parametrize("nq", [0, 1, 7, 9, 1000])
 def test_query_batch_sizes(hc, nq):
     n = 6000
