@@ -398,6 +398,10 @@ def run_hc(a):
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": traffic,
                 "algorithmic_bytes_per_launch": qbytes,
+                # DRAM bytes of the launch (ncu) over its duration: below `frac` when
+                # window rows are shared in L2 by queries answered together
+                "dram_frac": (traffic / (q_ms / 1000.0) / 1e9 / peaks["hbm_gbs"]
+                              if traffic else None),
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
                 if peak_src == "measured" else "fallback 6.8 TB/s"}
 
