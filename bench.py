@@ -330,7 +330,6 @@ def run_hc(a):
 
     workspace = torch.empty(hc.hc_query_ordered_workspace(a.nq), dtype=torch.uint8,
                             device="cuda")
-
     def query(idx, p=None):
         if a.input_order:
             hc.hc_query(idx, q, a.k, a.p if p is None else p, out_ids, out_dist, stream=stream)
@@ -344,7 +343,7 @@ def run_hc(a):
         ev[1].record(stream)
         query(idx)
         ev[2].record(stream)
-        idx.free()
+        idx.free(stream=stream)
 
     mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     for _ in range(a.warmup):

@@ -186,6 +186,13 @@ HC_API int hc_query_at(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k
  * caller makes sure no work using the index is still queued.  NULL is ok. */
 HC_API void hc_free(hc_index* idx);
 
+/* hc_free_async -- hc_free with the device memory released in stream order on
+ * cuda_stream: work on the index queued earlier on that stream completes
+ * first, and the call does not wait for other streams (the caller orders any
+ * other stream's work on the index before it).  Host memory of the index is
+ * released at once.  NULL is ok. */
+HC_API void hc_free_async(hc_index* idx, void* cuda_stream);
+
 /* hc_strerror -- static text for an hc_status value. */
 HC_API const char* hc_strerror(int status);
 

@@ -112,18 +112,20 @@ int check_params(const hc_build_params* p) {
 // The index arrays come from the stream-ordered pool; they are released in
 // order on the legacy default stream (after the work of every blocking
 // stream), so build/free cycles reuse pool memory without device syncs.
-void pool_free(void* p) {
-    if (p) cudaFreeAsync(p, cudaStreamLegacy);
+// stream-ordered release; the legacy stream waits for the work of every
+// blocking stream, which makes the default safe whatever stream used the index
+void pool_free(void* p, cudaStream_t s = cudaStreamLegacy) {
+    if (p) cudaFreeAsync(p, s);
 }
 
-void destroy(hc_index* x) {
+void destroy(hc_index* x, cudaStream_t s = cudaStreamLegacy) {
     if (!x) return;
-    pool_free(x->dim_map_dev);
-    pool_free(x->db_owned);
-    pool_free(x->keys_hi);
-    pool_free(x->keys_lo);
-    pool_free(x->ids);
-    pool_free(x->list_off_dev);
+    pool_free(x->dim_map_dev, s);
+    pool_free(x->db_owned, s);
+    pool_free(x->keys_hi, s);
+    pool_free(x->keys_lo, s);
+    pool_free(x->ids, s);
+    pool_free(x->list_off_dev, s);
     if (x->st_q) cudaFree(x->st_q);
     if (x->st_out) cudaFree(x->st_out);
     cudaGetLastError();
@@ -305,6 +307,10 @@ HC_API int hc_build_host(const void* db_host, const hc_build_params* params, voi
 }
 
 HC_API void hc_free(hc_index* idx) { destroy(idx); }
+
+HC_API void hc_free_async(hc_index* idx, void* cuda_stream) {
+    destroy(idx, static_cast<cudaStream_t>(cuda_stream));
+}
 
 HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
                     int32_t* out_ids_dev, void* out_dist_dev, void* cuda_stream) {

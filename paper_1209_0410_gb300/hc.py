@@ -84,6 +84,8 @@ def lib():
         L.hc_query_host.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]
         L.hc_free.argtypes = [_vp]
         L.hc_free.restype = None
+        L.hc_free_async.argtypes = [_vp, _vp]
+        L.hc_free_async.restype = None
         L.hc_index_describe.argtypes = [_vp, ctypes.POINTER(_IndexInfo), _vp]
         L.hc_index_copy_lists.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.hc_hilbert_keys.argtypes = [_vp, ctypes.c_int, _u64, _u32, _u32, _u32, _vp, _vp, _vp,
@@ -189,9 +191,13 @@ class Index:
         self.partitions = max(1, params.partitions)
         self.lists = self.curves * self.partitions
 
-    def free(self):
+    def free(self, stream=None):
+        """Release the index; with a stream, in stream order on it (hc_free_async)."""
         if self.handle:
-            lib().hc_free(self.handle)
+            if stream is None:
+                lib().hc_free(self.handle)
+            else:
+                lib().hc_free_async(self.handle, _stream(stream))
             self.handle = None
 
     def __del__(self):

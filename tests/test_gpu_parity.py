@@ -354,6 +354,26 @@ def test_query_ordered_equals_query(hc, dtype, nq, k, p, parts):
     idx.free()
 
 
+def test_free_async_on_streams(hc):
+    """Indexes built, queried and released in stream order on two streams
+    give the same answers as on the default stream."""
+    import torch
+    db, q = make_case(12000, 64, seed=8)
+    tdb, tq = dev(db), dev(q)
+    ref = hc.hc_query(hc.hc_build(tdb), tq, 10, 30)[0].clone()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for i in range(6):
+        s = streams[i % 2]
+        idx = hc.hc_build(tdb, stream=s)
+        ids, _ = hc.hc_query(idx, tq, 10, 30, stream=s)
+        idx.free(stream=s)
+        outs.append(ids)
+    sync()
+    for ids in outs:
+        assert torch.equal(ids, ref)
+
+
 def test_query_ordered_rejects_a_small_workspace(hc):
     import torch
     db, q = make_case(5000, 100, seed=2)
