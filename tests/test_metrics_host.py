@@ -1,0 +1,38 @@
+"""The quality metrics the benchmarks report, on hand-made CPU tensors:
+recall@10 counts returned entries whose distance is within the true 10th
+distance (ties count, padding does not), agreement is exact top-k equality."""
+import os
+import sys
+
+import pytest
+import torch
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+from paper_1209_0410_gb300 import learned  # noqa: E402
+import bench  # noqa: E402
+
+
+def case():
+    true_dist = torch.arange(1, 11, dtype=torch.int32).repeat(3, 1)   # 10th true distance = 10
+    ids = torch.arange(10, dtype=torch.int32).repeat(3, 1)
+    dist = torch.arange(1, 11, dtype=torch.int32).repeat(3, 1).clone()
+    dist[1, 5:] = torch.tensor([10, 10, 11, 12, 13], dtype=torch.int32)  # ties at 10 count
+    ids[2, 7:] = -1                                                       # padding
+    dist[2, 7:] = 2**31 - 1
+    return ids, dist, true_dist
+
+
+@pytest.mark.parametrize("fn", [learned.recall_at_10, bench.recall_at_10])
+def test_recall_at_10(fn):
+    ids, dist, true_dist = case()
+    # rows: 10/10, 7/10 (three beyond the 10th distance), 7/10 (three padded)
+    assert fn(ids, dist, true_dist) == pytest.approx((10 + 7 + 7) / 30)
+
+
+def test_agreement_is_exact_topk_equality():
+    ref = torch.arange(20, dtype=torch.int32).reshape(2, 10)
+    got = ref.clone()
+    assert learned.agreement(got, ref) == 1.0
+    got[1, 9] = 99
+    assert learned.agreement(got, ref) == 0.5
