@@ -36,3 +36,21 @@ def test_agreement_is_exact_topk_equality():
     assert learned.agreement(got, ref) == 1.0
     got[1, 9] = 99
     assert learned.agreement(got, ref) == 0.5
+
+
+def test_algorithmic_query_bytes_formula():
+    """Window rows and ids, the binary-search probes beyond 12 cached levels
+    (8 bytes each), the query row and the k results, from given positions."""
+    import types
+    import numpy as np
+    # two lists of 10 and 5000 entries; two queries
+    off = np.array([0, 10, 5010], dtype=np.uint64)
+    pos = torch.tensor([[3, 4000], [10, 100]], dtype=torch.int64)
+    fake = types.SimpleNamespace(hc_query_positions=lambda idx, q: pos,
+                                 hc_index_describe=lambda idx: ({}, off))
+    p, k, row = 4, 10, 128
+    qbytes, windows = bench.algorithmic_query_bytes(fake, None, None, p, k, row)
+    # windows: list 0 [0, 7) = 7 and [6, 10) = 4; list 1 [3996, 4004) and [96, 104) = 8 each
+    assert windows == 7 + 4 + 8 + 8
+    probes = max(0, 10 .bit_length() - 12) + max(0, 5000 .bit_length() - 12)   # 0 + 1
+    assert qbytes == windows * (row + 4) + 2 * (probes * 8 + row + k * 8)
