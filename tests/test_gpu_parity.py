@@ -374,6 +374,20 @@ def test_free_async_on_streams(hc):
         assert torch.equal(ids, ref)
 
 
+@pytest.mark.parametrize("d,curves,m", [(64, 10, 6), (128, 12, 10), (256, 16, 16)])
+def test_query_ordered_other_key_widths(hc, d, curves, m):
+    """Order keys from 48-, 80- and 128-bit extended-keys: any order gives
+    the same results."""
+    import torch
+    db, q = make_case(9001, 333, d=d, seed=d + m)
+    idx = hc.hc_build(dev(db), curves=curves, dims_per_curve=m)
+    ids_a, dist_a = hc.hc_query(idx, dev(q), 10, 25)
+    ids_b, dist_b = hc.hc_query_ordered(idx, dev(q), 10, 25)
+    sync()
+    assert torch.equal(ids_a, ids_b) and torch.equal(dist_a, dist_b)
+    idx.free()
+
+
 def test_query_ordered_rejects_a_small_workspace(hc):
     import torch
     db, q = make_case(5000, 100, seed=2)
