@@ -109,11 +109,10 @@ int check_params(const hc_build_params* p) {
 }
 
 
-// The index arrays come from the stream-ordered pool; they are released in
-// order on the legacy default stream (after the work of every blocking
-// stream), so build/free cycles reuse pool memory without device syncs.
-// stream-ordered release; the legacy stream waits for the work of every
-// blocking stream, which makes the default safe whatever stream used the index
+// The index arrays come from the stream-ordered pool and are released in
+// stream order, so build/free cycles reuse pool memory without device syncs.
+// By default on the legacy stream, which waits for the work of every blocking
+// stream (safe whatever stream used the index); hc_free_async names the stream.
 void pool_free(void* p, cudaStream_t s = cudaStreamLegacy) {
     if (p) cudaFreeAsync(p, s);
 }
