@@ -12,7 +12,8 @@ learned  N = 10M uint8, depth predictor trained on seeded queries (labels:
 serve    N = 50M uint8 resident, Poisson arrivals whose rate follows seeded
          on/off bursts times a sinusoid between 10k and 500k queries/s, k = 10,
          requests with p = 0 (learned depth, fixed-depth fallback), HBM-budget
-         admission: p50/p99 latency and sustained queries/s.
+         admission: p50/p99 latency and sustained queries/s; then a closed loop
+         of 4096-query requests for the server's capacity.
 partitions
          partitioned Hypercurves on one GPU (Sec. 4): N = 10M uint8 split into
          ell in {1, 2, 4, 8, 16, 32} in-HBM partitions, sequential depth
@@ -299,7 +300,30 @@ def run_serve(a):
     tp.join()
     wall = time.perf_counter() - wall0
     st = srv.stats()
+
+    # saturation: a closed loop keeps `outstanding` requests of sat_req queries
+    # in the server for about two seconds (capacity rather than offered load)
+    sat_req, outstanding = 4096, 16
+    sat_lat, sat_q = [], 0
+    pending = []
+    t_sat0 = time.perf_counter()
+    i = 0
+    while True:
+        while len(pending) < outstanding and time.perf_counter() - t_sat0 < 2.0:
+            s0 = (i * sat_req) % (pool.shape[0] - sat_req)
+            pending.append(srv.submit(0, pool[s0:s0 + sat_req], 10, 0))
+            i += 1
+        if not pending:
+            break
+        r = None
+        while r is None:
+            r = srv.poll(pending[0], 1_000_000, with_latency=True)
+        pending.pop(0)
+        sat_lat.append(r[2])
+        sat_q += sat_req
+    sat_wall = time.perf_counter() - t_sat0
     srv.close()
+    sat_lat = np.array(sat_lat) * 1e3
     lat = np.array([d[1] for d in done]) * 1e3
     served = len(done) * per_req
     # recall of the served answers (learned depths) on a sample
@@ -326,6 +350,11 @@ def run_serve(a):
                       "recall_at_10": rec, "recall_at_10_fixed_p128": r128,
                       "server": {k: int(v) for k, v in st.items()},
                       "mean_batch_queries": st["queries_done"] / max(1, st["batches_done"]),
+                      "saturation": {"qps": sat_q / sat_wall, "request_queries": sat_req,
+                                     "outstanding_requests": outstanding,
+                                     "seconds": sat_wall,
+                                     "latency_ms": {"p50": float(np.percentile(sat_lat, 50)),
+                                                    "p99": float(np.percentile(sat_lat, 99))}},
                       "setup_s": setup_s}})
     mlp.free()
     return 0
