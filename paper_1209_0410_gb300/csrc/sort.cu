@@ -125,13 +125,38 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const uint64_t* __restri
     __syncthreads();
     if (digits) {
         const uint8_t* dg = digits + start;
-#pragma unroll 4
-        for (uint32_t i = threadIdx.x; i < count; i += kThreads) atomicAdd(&h[__ldg(dg + i)], 1u);
+        // sixteen digits per 16-byte load where the tile starts aligned (one
+        // load per thread for a whole tile), the rest one byte at a time
+        uint32_t i0 = 0;
+        if ((reinterpret_cast<uintptr_t>(dg) & 15u) == 0) {
+            const uint32_t nv = count / 16;
+            const uint4* dv = reinterpret_cast<const uint4*>(dg);
+            for (uint32_t v = threadIdx.x; v < nv; v += kThreads) {
+                const uint4 x = __ldg(dv + v);
+                const uint32_t q[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) atomicAdd(&h[(q[j] >> (8 * b)) & 0xFFu], 1u);
+            }
+            i0 = nv * 16;
+        }
+        for (uint32_t i = i0 + threadIdx.x; i < count; i += kThreads)
+            atomicAdd(&h[__ldg(dg + i)], 1u);
     } else {
         const uint64_t* w = words + start;
-#pragma unroll 4
-        for (uint32_t i = threadIdx.x; i < count; i += kThreads)
-            atomicAdd(&h[(uint32_t)(__ldg(w + i) >> shift) & 0xFFu], 1u);
+        if (count == (uint32_t)kTile) {
+            // a whole tile: all sixteen loads of a thread in flight at once
+            constexpr int kPer = kTile / kThreads;
+            uint64_t x[kPer];
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) x[r] = __ldg(w + threadIdx.x + r * kThreads);
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) atomicAdd(&h[(uint32_t)(x[r] >> shift) & 0xFFu], 1u);
+        } else {
+            for (uint32_t i = threadIdx.x; i < count; i += kThreads)
+                atomicAdd(&h[(uint32_t)(__ldg(w + i) >> shift) & 0xFFu], 1u);
+        }
     }
     __syncthreads();
     counts[si.cnt_base + (uint64_t)threadIdx.x * si.ntiles + lt] = h[threadIdx.x];
