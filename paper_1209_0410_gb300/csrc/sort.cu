@@ -434,90 +434,142 @@ __global__ void __launch_bounds__(256) fixup_final_kernel(
 // In-place fix-up after a sort whose last pass wrote the final high words
 // and ids (affine ids, low words recomputed from rows).  Runs of equal
 // prefixes hi >> run_shift (ordered by id, i.e. by position) must end
-// ordered by (hi, low word, id).  A warp walks 32 records at a time; each run
-// that starts among them (at most kMaxRun = 32 records; a longer one sets
-// *long_run) is then sorted by the whole warp, one record per lane: lanes
-// whose high words tie compute their low words, every lane counts the run's
-// records below its own, and all lanes write after all have read.  Other
-// warps only read prefixes, which a permutation inside a run leaves
-// unchanged, so the in-place writes race with nothing.
-__global__ void __launch_bounds__(256) fixup_runs_kernel(uint64_t* hi, uint32_t* ids, int run_shift,
-                                                         RowKeys rows, uint32_t nseg,
-                                                         const SegInfo* __restrict__ segs,
-                                                         uint32_t* __restrict__ long_run) {
-    static_assert(kMaxRun == 32, "one run record per lane");
+// ordered by (hi, low word, id).  Two kernels:
+//   find_runs  streams the high words (one tile per block, eight 32-record
+//              chunks of a warp loaded at once) and appends the position and
+//              segment of every run start to a list, one atomic per block;
+//   sort_runs  gives each listed run to one warp, one record per lane (at
+//              most kMaxRun = 32 records; a longer one sets *long_run):
+//              lanes whose high words tie compute their low words, every lane
+//              counts the run's records below its own, and all lanes write
+//              after all have read.
+// A warp reading past its run's end sees only prefixes, which a permutation
+// inside another run leaves unchanged, so the in-place writes race with
+// nothing.
+constexpr int kFindWarps = 8;
+constexpr int kFindChunks = kTile / 32 / kFindWarps;   // 16 chunks of 32 records per warp
+constexpr int kFindBatch = 8;                          // chunks loaded at once
+
+__global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
+    const uint64_t* __restrict__ hi, int run_shift, uint32_t nseg,
+    const SegInfo* __restrict__ segs, uint64_t* __restrict__ run_pos,
+    uint32_t* __restrict__ run_seg, unsigned long long* __restrict__ nruns) {
+    static_assert(kFindChunks % kFindBatch == 0, "whole batches");
+    __shared__ uint32_t masks[kFindWarps][kFindChunks];
+    __shared__ uint32_t wbase[kFindWarps];
+    __shared__ unsigned long long bbase;
     SegInfo si;
     uint32_t seg, lt, count;
     uint64_t start;
     tile_of(nseg, segs, si, seg, lt, start, count);
     const uint64_t seg_end = si.start + si.len;
-    const uint32_t curve = seg % rows.P.curves;
     const int lane = threadIdx.x & 31;
-    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    // kBatch chunks of 32 records per warp have their words loaded at once
-    constexpr int kBatch = 4;
-    for (uint32_t b0 = warp * 32; b0 < count; b0 += kBatch * nwarps * 32) {
-        uint64_t hv[kBatch], hn[kBatch], hp[kBatch];
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t found = 0;
+    for (int c0 = 0; c0 < kFindChunks; c0 += kFindBatch) {
+        // a chunk's words, plus the word before it (lane 0) or after it (lane 31)
+        uint64_t hv[kFindBatch], halo[kFindBatch];
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) {
-            const uint32_t base = b0 + (uint32_t)j * nwarps * 32;
-            const uint64_t i = start + base + lane;
-            const bool ok = base + lane < count;
-            hv[j] = ok ? hi[i] : 0;
-            hn[j] = (ok && i + 1 < seg_end) ? hi[i + 1] : 0;
-            hp[j] = (ok && lane == 0 && i > si.start) ? hi[i - 1] : 0;
+        for (int j = 0; j < kFindBatch; ++j) {
+            const uint32_t off = (warp * kFindChunks + (uint32_t)(c0 + j)) * 32 + (uint32_t)lane;
+            const uint64_t i = start + off;
+            const bool ok = off < count;
+            hv[j] = ok ? __ldg(hi + i) : 0;
+            uint64_t h = 0;
+            if (ok && lane == 0 && i > si.start) h = __ldg(hi + i - 1);
+            if (ok && lane == 31 && i + 1 < seg_end) h = __ldg(hi + i + 1);
+            halo[j] = h;
         }
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) {
-            const uint32_t base = b0 + (uint32_t)j * nwarps * 32;
-            const uint64_t i = start + base + lane;
-            const bool ok = base + lane < count;
+        for (int j = 0; j < kFindBatch; ++j) {
+            const uint32_t off = (warp * kFindChunks + (uint32_t)(c0 + j)) * 32 + (uint32_t)lane;
+            const uint64_t i = start + off;
+            const bool ok = off < count;
             const uint64_t key = hv[j] >> run_shift;
-            // every lane takes part in the shuffle; lane 0 then uses its own load
+            // every lane takes part in both shuffles; the end lanes then use their halo
             const uint64_t up = __shfl_up_sync(0xffffffffu, hv[j], 1);
-            const uint64_t prev = lane == 0 ? hp[j] : up;
-            const bool run_start = ok && i + 1 < seg_end && (hn[j] >> run_shift) == key &&
+            const uint64_t dn = __shfl_down_sync(0xffffffffu, hv[j], 1);
+            const uint64_t prev = lane == 0 ? halo[j] : up;
+            const uint64_t next = lane == 31 ? halo[j] : dn;
+            const bool run_start = ok && i + 1 < seg_end && (next >> run_shift) == key &&
                                    !(i > si.start && (prev >> run_shift) == key);
-            uint32_t starts = __ballot_sync(0xffffffffu, run_start);
-            while (starts) {
-                const int src = __ffs(starts) - 1;
-                starts &= starts - 1;
-                const uint64_t rs = start + base + src;
-                const uint64_t rkey = __shfl_sync(0xffffffffu, key, src);
-                // the run's records, one per lane, words and ids loaded together
-                const uint64_t e = rs + lane;
-                const bool inseg = e < seg_end;
-                const uint64_t he = inseg ? hi[e] : ~0ull;
-                const uint32_t de = inseg ? ids[e] : 0xFFFFFFFFu;
-                const bool in = inseg && (he >> run_shift) == rkey;
-                const uint32_t inmask = __ballot_sync(0xffffffffu, in);
-                const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
-                if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == rkey) {
-                    if (lane == 0) atomicOr(long_run, 1u);
-                    continue;
-                }
-                const bool mine = (uint32_t)lane < len;
-                const uint64_t h = mine ? he : ~0ull;
-                const uint32_t d = mine ? de : 0xFFFFFFFFu;
-                const uint32_t peers = __match_any_sync(0xffffffffu, h);
-                const uint64_t l = (mine && __popc(peers) > 1)
-                                       ? row_key_lo(rows.db, rows.row_bytes, rows.P, d, curve)
-                                       : 0;
-                uint32_t rank = 0;
-                for (uint32_t u = 0; u < len; ++u) {
-                    const uint64_t hu = __shfl_sync(0xffffffffu, h, (int)u);
-                    const uint64_t lu = __shfl_sync(0xffffffffu, l, (int)u);
-                    const uint32_t du = __shfl_sync(0xffffffffu, d, (int)u);
-                    rank += (hu < h || (hu == h && (lu < l || (lu == l && du < d)))) ? 1u : 0u;
-                }
-                __syncwarp();
-                if (mine) {
-                    hi[rs + rank] = h;
-                    ids[rs + rank] = d;
-                }
-                __syncwarp();
-            }
+            const uint32_t starts = __ballot_sync(0xffffffffu, run_start);
+            if (lane == 0) masks[warp][c0 + j] = starts;
+            found += (uint32_t)__popc(starts);
         }
+    }
+    if (lane == 0) wbase[warp] = found;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t total = 0;
+        for (int w = 0; w < kFindWarps; ++w) {
+            const uint32_t c = wbase[w];
+            wbase[w] = total;
+            total += c;
+        }
+        bbase = total ? atomicAdd(nruns, (unsigned long long)total) : 0ull;
+    }
+    __syncthreads();
+    uint64_t slot = bbase + wbase[warp];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int c = 0; c < kFindChunks; ++c) {
+        const uint32_t m = masks[warp][c];
+        if ((m >> lane) & 1u) {
+            const uint64_t r = slot + (uint32_t)__popc(m & lt_mask);
+            run_pos[r] = start + (warp * kFindChunks + (uint32_t)c) * 32 + (uint32_t)lane;
+            run_seg[r] = seg;
+        }
+        slot += (uint32_t)__popc(m);
+    }
+}
+
+__global__ void __launch_bounds__(256) sort_runs_kernel(
+    uint64_t* hi, uint32_t* ids, int run_shift, RowKeys rows, const SegInfo* __restrict__ segs,
+    const uint64_t* __restrict__ run_pos, const uint32_t* __restrict__ run_seg,
+    const unsigned long long* __restrict__ nruns, uint32_t* __restrict__ long_run) {
+    static_assert(kMaxRun == 32, "one run record per lane");
+    const int lane = threadIdx.x & 31;
+    const uint64_t n = *nruns;
+    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t r = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n;
+         r += nw) {
+        const uint64_t rs = __ldg(run_pos + r);
+        const uint32_t seg = __ldg(run_seg + r);
+        const uint64_t seg_end = segs[seg].start + segs[seg].len;
+        const uint32_t curve = seg % rows.P.curves;
+        // the run's records, one per lane, words and ids loaded together
+        const uint64_t e = rs + lane;
+        const bool inseg = e < seg_end;
+        const uint64_t he = inseg ? hi[e] : ~0ull;
+        const uint32_t de = inseg ? ids[e] : 0xFFFFFFFFu;
+        const uint64_t rkey = __shfl_sync(0xffffffffu, he, 0) >> run_shift;
+        const bool in = inseg && (he >> run_shift) == rkey;
+        const uint32_t inmask = __ballot_sync(0xffffffffu, in);
+        const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
+        if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == rkey) {
+            if (lane == 0) atomicOr(long_run, 1u);
+            continue;
+        }
+        const bool mine = (uint32_t)lane < len;
+        const uint64_t h = mine ? he : ~0ull;
+        const uint32_t d = mine ? de : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, h);
+        const uint64_t l = (mine && __popc(peers) > 1)
+                               ? row_key_lo(rows.db, rows.row_bytes, rows.P, d, curve)
+                               : 0;
+        uint32_t rank = 0;
+        for (uint32_t u = 0; u < len; ++u) {
+            const uint64_t hu = __shfl_sync(0xffffffffu, h, (int)u);
+            const uint64_t lu = __shfl_sync(0xffffffffu, l, (int)u);
+            const uint32_t du = __shfl_sync(0xffffffffu, d, (int)u);
+            rank += (hu < h || (hu == h && (lu < l || (lu == l && du < d)))) ? 1u : 0u;
+        }
+        __syncwarp();
+        if (mine) {
+            hi[rs + rank] = h;
+            ids[rs + rank] = d;
+        }
+        __syncwarp();
     }
 }
 
@@ -550,7 +602,7 @@ Layout make_layout(const SortProblem& p) {
     L.off_counts = o;  o = align_up(o + sizeof(uint32_t) * (L.ncounts ? L.ncounts : 1));
     L.off_totals = o;  o = align_up(o + sizeof(uint32_t) * 256 * (L.nseg ? L.nseg : 1));
     L.off_segs = o;    o = align_up(o + sizeof(SegInfo) * (L.nseg ? L.nseg : 1));
-    L.off_flag = o;    o = align_up(o + sizeof(uint32_t));
+    L.off_flag = o;    o = align_up(o + 16);   // flag word; run count at +8
     L.off_digits = o;  o = align_up(o + L.total);
     L.bytes = o;
     return L;
@@ -662,11 +714,20 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             wn ^= 1;
             pn ^= 1;
         }
-        if (cudaMemsetAsync(flag, 0, sizeof(uint32_t), s) != cudaSuccess) return HC_ERR_CUDA;
+        // the flag word, then (8 bytes on) the run count of the in-place fix-up
+        unsigned long long* nruns = reinterpret_cast<unsigned long long*>(base + L.off_flag + 8);
+        if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return HC_ERR_CUDA;
         if (in_place) {
             if (cw != p.out_hi) return HC_ERR_STATE;
-            fixup_runs_kernel<<<L.ntiles, 256, 0, s>>>(p.out_hi, p.out_ids, 8 * skip, p.rows,
-                                                       L.nseg, segs, flag);
+            // both position buffers are free once the last pass has run: at
+            // most total / 2 runs (two records or more each) fit in either
+            uint64_t* run_pos = reinterpret_cast<uint64_t*>(pa);
+            uint32_t* run_seg = pb;
+            find_runs_kernel<<<L.ntiles, kFindWarps * 32, 0, s>>>(p.out_hi, 8 * skip, L.nseg, segs,
+                                                                run_pos, run_seg, nruns);
+            sort_runs_kernel<<<grid_stride_blocks(L.total / 64), 256, 0, s>>>(
+                p.out_hi, p.out_ids, 8 * skip, p.rows, segs, run_pos, run_seg, nruns, flag);
+            count_launches(1);
         } else {
             if (cw != wtmp) return HC_ERR_STATE;
             fixup_final_kernel<<<L.ntiles, 256, 0, s>>>(
