@@ -162,26 +162,42 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const uint64_t* __restri
     counts[si.cnt_base + (uint64_t)threadIdx.x * si.ntiles + lt] = h[threadIdx.x];
 }
 
-// grid (256 digits, segments): exclusive scan of one digit row over the tiles
-__global__ void __launch_bounds__(kThreads) scan_kernel(const SegInfo* __restrict__ segs,
-                                                        uint32_t* __restrict__ counts,
-                                                        uint32_t* __restrict__ totals) {
-    __shared__ uint32_t warp_sums[kWarps];
+// grid (256 digits, segments): exclusive scan of one digit row over the tiles.
+// Small blocks (sixteen resident per SM) walk the row in
+// chunks of kScanPer consecutive tiles per thread, every load of a chunk in
+// flight, with the running total carried from chunk to chunk.
+constexpr int kScanThreads = 128;
+constexpr int kScanPer = 8;
+
+__global__ void __launch_bounds__(kScanThreads, 16) scan_kernel(const SegInfo* __restrict__ segs,
+                                                                uint32_t* __restrict__ counts,
+                                                                uint32_t* __restrict__ totals) {
+    constexpr int kNW = kScanThreads / 32;
+    __shared__ uint32_t warp_sums[kNW];
     const SegInfo si = segs[blockIdx.y];
     const uint32_t digit = blockIdx.x;
     uint32_t* row = counts + si.cnt_base + (uint64_t)digit * si.ntiles;
     const uint32_t T = si.ntiles;
-    const uint32_t per = (T + kThreads - 1) / kThreads;
-    const uint32_t b = min(T, threadIdx.x * per), e = min(T, b + per);
-    uint32_t sum = 0;
-    for (uint32_t i = b; i < e; ++i) sum += row[i];
-    uint32_t run = block_exclusive_scan(sum, warp_sums);
-    if (threadIdx.x == kThreads - 1) totals[(uint64_t)blockIdx.y * 256 + digit] = run + sum;
-    for (uint32_t i = b; i < e; ++i) {
-        const uint32_t c = row[i];
-        row[i] = run;
-        run += c;
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < T; c0 += (uint32_t)(kScanThreads * kScanPer)) {
+        const uint32_t b = c0 + threadIdx.x * kScanPer;
+        uint32_t v[kScanPer], sum = 0;
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            v[j] = b + j < T ? row[b + j] : 0u;
+            sum += v[j];
+        }
+        uint32_t run = carry + block_exclusive_scan<kNW>(sum, warp_sums);
+        const uint32_t chunk_total = warp_sums[kNW - 1];   // inclusive total of the last warp
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            if (b + j < T) row[b + j] = run;
+            run += v[j];
+        }
+        carry += chunk_total;
+        __syncthreads();   // the next chunk's scan rewrites warp_sums
     }
+    if (threadIdx.x == 0) totals[(uint64_t)blockIdx.y * 256 + digit] = carry;
 }
 
 // One scatter tile in shared memory: the words and positions of the tile in
@@ -703,7 +719,7 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             const bool first = t == 8 + skip;
             hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cw, first ? nullptr : dgt, shift, L.nseg,
                                                       segs, counts);
-            scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
+            scan_kernel<<<scan_grid, kScanThreads, 0, s>>>(segs, counts, totals);
             scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(
                 cw, cp, wb[wn], pd, shift, L.nseg, segs, counts, totals,
                 (last && in_place) ? p.id_base_dev : nullptr, last ? nullptr : dgt);
@@ -765,7 +781,7 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
         if (L.ntiles) {
             hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cur_w, have_digits ? dgt : nullptr, shift,
                                                       L.nseg, segs, counts);
-            scan_kernel<<<scan_grid, kThreads, 0, s>>>(segs, counts, totals);
+            scan_kernel<<<scan_grid, kScanThreads, 0, s>>>(segs, counts, totals);
             uint64_t* wd = wbuf[wnext];
             uint32_t* pd = pbuf[pnext];
             scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(
