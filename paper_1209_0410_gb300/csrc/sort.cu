@@ -14,7 +14,8 @@
 // path sorts only the top bytes of the high word (hi_skip low bytes left out)
 // and a fix-up orders the short runs of equal prefixes by (high word, low
 // word, id).  For an index with affine ids and no stored low words the last
-// pass writes the final high words and ids and the fix-up works in place;
+// pass writes the final high words and ids and the fix-up works in place
+// (find_runs lists the run starts, sort_runs orders each run with one warp);
 // a run longer than 32 sends the caller back for a sort by every byte.
 //
 // Per pass, three kernels, none of which waits on another block:
