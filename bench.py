@@ -68,7 +68,8 @@ def parse_args():
     ap.add_argument("--p", type=int, default=128)
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--dtype", choices=["u8", "f32"], default="u8")
-    ap.add_argument("--sweep", default="32,128,512", help="query-only p sweep ('' = none)")
+    ap.add_argument("--sweep", default="32,64,128,256,512",
+                    help="query-only p sweep ('' = none)")
     ap.add_argument("--recall-sample", type=int, default=2000)
     ap.add_argument("--input-order", action="store_true",
                     help="answer the queries in input order (hc_query) instead of curve-0 key "
@@ -236,6 +237,18 @@ def recall_at_10(ids, dist, true_dist):
     kth = true_dist[:, 9:10].to(torch.float64)
     ok = (dist[:, :10].to(torch.float64) <= kth) & (ids[:, :10] >= 0)
     return float(ok.sum(dim=1).clamp(max=10).to(torch.float64).mean().item() / 10.0)
+
+
+def fixed_recall_point(sweep, ref_p):
+    """The smallest swept depth whose recall@10 reaches the recall at ref_p (the
+    metric's fixed recall), with its query throughput; None without ref_p."""
+    ref = [e for e in sweep if e["p"] == ref_p]
+    if not ref:
+        return None
+    target = ref[0]["recall_at_10"]
+    best = min((e for e in sweep if e["recall_at_10"] >= target), key=lambda e: e["p"])
+    return {"p": best["p"], "recall_at_10": best["recall_at_10"],
+            "target_recall_at_10": target, "query_qps": best["query_qps"]}
 
 
 # ----------------------------------------------------------- CPU oracle leg
@@ -438,6 +451,7 @@ def run_hc(a):
                           "recall_at_10": recall_at_10(out_ids[:rs], out_dist[:rs], tdist),
                           "hbm_frac": qb / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"]})
         cfg["query_sweep"] = sweep
+        cfg["fixed_recall_point"] = fixed_recall_point(sweep, a.p)
     idx.free()
 
     e2e = None

@@ -54,3 +54,17 @@ def test_algorithmic_query_bytes_formula():
     assert windows == 7 + 4 + 8 + 8
     probes = max(0, 10 .bit_length() - 12) + max(0, 5000 .bit_length() - 12)   # 0 + 1
     assert qbytes == windows * (row + 4) + 2 * (probes * 8 + row + k * 8)
+
+
+def test_fixed_recall_point_picks_smallest_depth_reaching_reference():
+    sweep = [{"p": 32, "recall_at_10": 0.50, "query_qps": 9e7},
+             {"p": 64, "recall_at_10": 0.61, "query_qps": 5e7},
+             {"p": 128, "recall_at_10": 0.61, "query_qps": 2.4e7},
+             {"p": 256, "recall_at_10": 0.70, "query_qps": 1.2e7}]
+    pt = bench.fixed_recall_point(sweep, 128)
+    assert pt["p"] == 64 and pt["query_qps"] == 5e7
+    assert pt["target_recall_at_10"] == 0.61
+    # the reference depth itself when nothing smaller reaches it
+    sweep[1]["recall_at_10"] = 0.60
+    assert bench.fixed_recall_point(sweep, 128)["p"] == 128
+    assert bench.fixed_recall_point(sweep, 100) is None
