@@ -59,7 +59,7 @@ int dev_alloc_async(void** p, size_t bytes, cudaStream_t s) {
 }
 
 void keep_pool_memory() {
-    // stream-ordered scratch is returned to the pool, not to the driver,
+    // stream-ordered scratch stays in the memory pool (not released to CUDA)
     // between builds of this process
     static std::atomic<bool> done{false};
     if (done.exchange(true)) return;
