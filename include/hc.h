@@ -90,21 +90,25 @@ typedef struct {
 
 /*
  * hc_build -- Algorithm 1 on the GPU: for every partition and curve, the
- * extended-key of each row's projection, then a stable device radix sort of
- * (key, id), giving one list sorted by (key, id) per (partition, curve).
+ * extended-key of each row's projection, then a device sort of (key, id),
+ * giving one list sorted by (key, id) per (partition, curve).  For
+ * 16-coordinate curves the sort is a sample sort of the high key words
+ * (buckets of about 2048 entries between splitters drawn from a sample,
+ * each bucket sorted in shared memory; a tie of high words is broken by the
+ * low words recomputed from the rows, then by id); shorter keys are radix-
+ * sorted by every key byte.
  *   db_dev   n x d rows (uint8 or float32 per params->dtype), 16-byte aligned.
  *            NOT copied: the index keeps the pointer, so the caller keeps the
  *            buffer alive and unchanged until hc_free.
  *   out      receives the new index (owned by the library; free with hc_free).
  * The library allocates the index arrays (12 bytes per row and curve for
  * 16-coordinate curves, whose lists keep the high key word and the id; 20
- * bytes otherwise) and, during the call, scratch of about 25 bytes per row
- * and curve (33 when low words are kept; more if a run of over 32 equal
- * 56-bit key prefixes makes it sort by every key byte); HC_ERR_OOM
- * if that fails.  Work is queued on cuda_stream; the call waits on that stream
- * once, after the sort, to read the sort's device status (a run of equal
- * 56-bit key prefixes longer than 32 makes it sort again by every key byte).
- * The index may be used by later work on the same stream.
+ * bytes otherwise) and, during the call, stream-ordered scratch of about 27
+ * bytes per row and curve (33 when low words are kept); HC_ERR_OOM if that
+ * fails.  All work is queued on cuda_stream and the call returns without
+ * waiting on it; the index may be used by later work on the same stream (or
+ * on another stream after an event).  On an error return nothing of the
+ * index remains (the call then waits for its queued work before freeing).
  */
 HC_API int hc_build(const void* db_dev, const hc_build_params* params, void* cuda_stream,
                     hc_index** out);
@@ -269,8 +273,13 @@ HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
  *   overlap on the GPU (different streams, or different host threads on the
  *   same device) race on that array and give wrong results: order them.
  *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture begins.
+ *   (cudaGetSymbolAddress) with that device current, and that lookup is when
+ *   the device loads the array (CUDA loads modules lazily).  Make that first
+ *   call -- a call with seg_off_host[nseg] == 0 does the set-up and nothing
+ *   else -- before any stream capture begins and before the caller's memory
+ *   manager reserves the device's memory.  cuda_stream must belong to the
+ *   current device.  cudaDeviceReset is not supported: the address looked up
+ *   before it is not valid after it.
  *   Unlike hc_sort_keys, the call is asynchronous on cuda_stream: the sorted
  *   arrays, and the scratch, are in use until the stream reaches it.
  */
@@ -459,7 +468,9 @@ typedef struct {
  * hc_serve_create(_ex) -- starts a server over n_idx built indexes (borrowed:
  * they must outlive the server).  hbm_budget >= 4096 bytes of device memory
  * (plus the same of pinned host memory) are allocated now.  params may be
- * NULL (defaults).  HC_ERR_OOM if the budget cannot be allocated.
+ * NULL (defaults).  HC_ERR_OOM if the budget cannot be allocated.  The call
+ * first waits for all work queued on the device (the server's own streams do
+ * not wait on the streams that built the indexes).
  */
 HC_API int hc_serve_create(hc_index* const* idx, uint32_t n_idx, uint64_t hbm_budget,
                            hc_server** out);

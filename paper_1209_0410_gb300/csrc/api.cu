@@ -168,21 +168,33 @@ int build_index(hc_index* x, cudaStream_t s) {
         return rc;
     if ((rc = dev_alloc_async((void**)&x->ids, sizeof(uint32_t) * total, s))) return rc;
 
-    SortProblem sp;
-    sp.seg_off = x->list_off;
-    sp.seg_off_dev = x->list_off_dev;
-    sp.key_bits = 8 * P.dims_per_curve;
-    sp.allow_sync = true;
-    sp.hi_skip = 1;   // runs of equal top-56-bit prefixes are a few records long
-    sp.out_hi = x->keys_hi;
-    sp.out_lo = x->keys_lo;
-    sp.out_ids = x->ids;
     // ids are implied by the slot: list L holds its partition's rows in id
     // order before the sort, so id = partition start + (slot - list start)
     std::vector<uint64_t> id_base(x->lists);
     for (uint32_t L = 0; L < x->lists; ++L)
         id_base[L] = partition_start(L / P.curves, P.n, parts);
-    const size_t sort_bytes = sort_scratch_bytes(sp);
+    // 16-coordinate keys: a sample sort of the high words, ties of the high
+    // word broken by low words recomputed from the rows.  Shorter keys: the
+    // radix sort by every key byte (the low words are stored).  Neither
+    // waits on the host.
+    SortProblem sp;
+    BucketSortProblem bp;
+    size_t sort_bytes;
+    if (keep_lo) {
+        sp.seg_off = x->list_off;
+        sp.seg_off_dev = x->list_off_dev;
+        sp.key_bits = 8 * P.dims_per_curve;
+        sp.allow_sync = false;
+        sp.out_hi = x->keys_hi;
+        sp.out_lo = x->keys_lo;
+        sp.out_ids = x->ids;
+        sort_bytes = sort_scratch_bytes(sp);
+    } else {
+        bp.seg_off = x->list_off;
+        bp.out_hi = x->keys_hi;
+        bp.out_ids = x->ids;
+        sort_bytes = bucket_sort_scratch_bytes(bp.seg_off);
+    }
     const size_t key_bytes = ((sizeof(uint64_t) * (keep_lo ? 2 : 1) * total) + 255) & ~(size_t)255;
     const size_t base_bytes = (sizeof(uint64_t) * x->lists + 255) & ~(size_t)255;
     void* scratch = nullptr;
@@ -198,31 +210,17 @@ int build_index(hc_index* x, cudaStream_t s) {
     if (rc == HC_OK)
         rc = status_of(upload_small(id_base_dev, id_base.data(), sizeof(uint64_t) * x->lists, s));
     if (rc == HC_OK) {
-        sp.hi = hi0;
-        sp.lo = lo0;
-        sp.ids = nullptr;
-        sp.id_base_dev = id_base_dev;
-        sp.rows = RowKeys{x->db, x->row_bytes, view_of(x).P};
-        rc = sort_segments(sp, sort_scratch, s);
-    }
-    if (rc == kSortNeedsLow) {
-        // a run of equal high words too long for the fix-up: compute the low
-        // words and sort by every key byte (the high words are rewritten
-        // with the same values; the sorted low words are dropped)
-        uint64_t* lo_buf = nullptr;
-        rc = dev_alloc_async((void**)&lo_buf, sizeof(uint64_t) * 2 * total, s);
-        if (rc == HC_OK) {
-            BuildKeysArgs kb = ka;
-            kb.lo = lo_buf;
-            rc = status_of(launch_build_keys(kb, s));
-            if (rc == HC_OK) {
-                sp.lo = lo_buf;
-                sp.out_lo = lo_buf + total;
-                sp.allow_sync = false;
-                rc = sort_segments(sp, sort_scratch, s);
-            }
-            const int lrc = status_of(cudaFreeAsync(lo_buf, s));
-            if (rc == HC_OK) rc = lrc;
+        if (keep_lo) {
+            sp.hi = hi0;
+            sp.lo = lo0;
+            sp.ids = nullptr;
+            sp.id_base_dev = id_base_dev;
+            rc = sort_segments(sp, sort_scratch, s);
+        } else {
+            bp.keys = hi0;
+            bp.id_base_dev = id_base_dev;
+            bp.rows = RowKeys{x->db, x->row_bytes, view_of(x).P};
+            rc = bucket_sort(bp, sort_scratch, s);
         }
     }
     const int frc = status_of(cudaFreeAsync(scratch, s));

@@ -81,6 +81,22 @@ size_t sort_scratch_bytes(const SortProblem& p);
 // Enqueues the whole sort on s using the given scratch (>= sort_scratch_bytes).
 int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s);
 
+// Sample sort of high key words by segment (bucket_sort.cu), for indexes of
+// 16-coordinate curves whose ids are affine in the list position and whose
+// low words are recomputed from the rows: record i of segment s has id
+// id_base[s] + i, and the segments leave ordered by (high word, low word,
+// id).  Everything runs on the stream without a host wait.
+struct BucketSortProblem {
+    uint64_t* keys = nullptr;          // device, high words by segment; used as scratch
+    std::vector<uint64_t> seg_off;     // host, nseg+1
+    const uint64_t* id_base_dev = nullptr;   // device, nseg
+    RowKeys rows{};
+    uint64_t* out_hi = nullptr;        // device, total records
+    uint32_t* out_ids = nullptr;
+};
+size_t bucket_sort_scratch_bytes(const std::vector<uint64_t>& seg_off);
+int bucket_sort(const BucketSortProblem& p, void* scratch, cudaStream_t s);
+
 // Small host tables written to device memory by a kernel that takes them
 // as a by-value parameter, so that no pageable copy (and its implicit
 // stream synchronisation) sits on the build path.

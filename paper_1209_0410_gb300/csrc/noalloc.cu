@@ -20,9 +20,12 @@ constexpr size_t kNoAllocScratchBytes = 10ull << 20;  // 10 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device.  In host
-// code the array's name only stands in for the symbol; handing it to a kernel
-// would not give the device address.
+// Device address of g_noalloc_scratch, looked up once per device (the first
+// call on a device, with that device current).  In host code the array's
+// name only stands in for the symbol; handing it to a kernel would not give
+// the device address.  The module holding the array is loaded on a device
+// by that first lookup (lazy module loading), so that is when the array's
+// memory is taken; the cached address does not survive cudaDeviceReset.
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
@@ -70,11 +73,11 @@ extern "C" HC_API int hc_sort_keys_noalloc(uint64_t* hi_dev, uint64_t* lo_dev, u
         if (seg_off_host[i + 1] < seg_off_host[i]) return HC_ERR_ARG;
     const uint64_t total = seg_off_host[nseg];
     if (total > kNoAllocMaxRecords) return HC_ERR_ARG;
-    if (total == 0) return HC_OK;
-    if (!on_device(hi_dev) || !on_device(lo_dev) || !on_device(ids_dev)) return HC_ERR_ARG;
-
+    // the per-device set-up comes first, so that a call with no records does it
     void* base = nullptr;
     if (int rc = scratch_address(&base)) return rc;
+    if (total == 0) return HC_OK;
+    if (!on_device(hi_dev) || !on_device(lo_dev) || !on_device(ids_dev)) return HC_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
     // scratch layout: sorted outputs | segment offsets | sort working area

@@ -355,6 +355,9 @@ HC_API int hc_serve_create_ex(hc_index* const* idx, uint32_t n_idx, uint64_t hbm
     if (P.streams < 1 || P.streams > 16 || P.max_batch_queries < 1 || P.default_p < 1 ||
         P.default_p > (1u << 30))
         return HC_ERR_ARG;
+    // the server's streams do not wait on the streams that built the
+    // indexes: let every build queued so far finish first
+    if (cudaDeviceSynchronize() != cudaSuccess) return HC_ERR_CUDA;
     hc_server* S = new (std::nothrow) hc_server();
     if (!S) return HC_ERR_OOM;
     S->idx.assign(idx, idx + n_idx);

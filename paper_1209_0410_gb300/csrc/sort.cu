@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "hc_block.cuh"
 #include "hc_internal.h"
 
 namespace hc {
@@ -34,7 +35,6 @@ namespace hc {
 namespace {
 
 constexpr int kThreads = 256;                 // histogram / scan / gather blocks
-constexpr int kWarps = kThreads / 32;
 constexpr int kTile = 4096;                    // records per tile
 // scatter blocks: 16 warps of 256 consecutive records each (8 rounds of 32)
 constexpr int kSThreads = 512;
@@ -81,33 +81,6 @@ __device__ __forceinline__ void tile_of(uint32_t nseg, const SegInfo* segs, SegI
     start = si.start + (uint64_t)lt * kTile;
     const uint64_t left = si.len - (uint64_t)lt * kTile;
     count = (uint32_t)(left < (uint64_t)kTile ? left : (uint64_t)kTile);
-}
-
-// Exclusive scan of one value per thread over a block of NW warps.
-template <int NW = kWarps>
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < NW ? warp_sums[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < NW; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < NW) warp_sums[lane] = w;  // inclusive warp totals
-    }
-    __syncthreads();
-    const uint32_t before = warp ? warp_sums[warp - 1] : 0u;
-    __syncthreads();  // warp_sums may be reused by the caller
-    return before + x - v;
 }
 
 // digits (null: read the words): this pass's digit of every record, one byte
@@ -218,19 +191,6 @@ struct ScatterSmem {
     uint64_t gbase[256];
     uint32_t warp_sums[kSWarps];
 };
-
-// Lanes of the warp whose 8-bit digit equals this lane's (warp-level
-// multisplit by ballots, one per digit bit).
-__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
-    uint32_t peers = 0xffffffffu;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const bool bit = (d >> b) & 1u;
-        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-        peers &= bit ? bal : ~bal;
-    }
-    return peers;
-}
 
 // Tile ranking: warp w owns records [256 w, 256 w + 256), lane l of round r
 // holds record 256 w + 32 r + l (coalesced loads).  Each round ranks its 32

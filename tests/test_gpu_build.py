@@ -1,0 +1,129 @@
+"""Algorithm 1's sorted lists from hc_build's sample sort, against the oracle.
+
+Every list is cut into buckets of about 2048 entries by splitters taken from
+a sample of its keys (itself sorted through a smaller sub-sample), and every
+bucket is sorted in shared memory; buckets too large for that, or holding a
+run of more than 32 entries equal in their sorted bits, are sorted by a
+fallback kernel.  The cases below reach each of those paths at sizes the
+oracle builds in seconds, and the lists must equal the oracle's bit for bit
+(keys, low words recomputed from the rows, ids).  The last case checks that
+hc_build returns without waiting for its stream.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from helpers import dev, u64
+from oracle import oracle as O
+from paper_1209_0410_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1209_0410_gb300 import hc as _hc
+    _hc.lib()
+    return _hc
+
+
+def sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def assert_lists_equal(hc, idx, oidx):
+    hi, lo, ids, off = hc.hc_index_copy_lists(idx)
+    sync()
+    assert np.array_equal(off, oidx.list_off)
+    gh, gl = u64(hi), u64(lo)
+    gi = ids.cpu().numpy().view(np.uint32)
+    for L in range(len(off) - 1):
+        a, b = int(off[L]), int(off[L + 1])
+        assert np.array_equal(gh[a:b], oidx.keys_hi[a:b]), "high words of list %d" % L
+        assert np.array_equal(gl[a:b], oidx.keys_lo[a:b]), "low words of list %d" % L
+        assert np.array_equal(gi[a:b], oidx.ids[a:b]), "ids of list %d" % L
+
+
+@pytest.mark.parametrize("n,parts", [(600_000, 1), (900_000, 3), (3_000_000, 1)])
+def test_sampled_levels_bit_exact(hc, n, parts):
+    """Lists long enough for all three levels: 600k entries give 293 buckets
+    split by a 4,688-key sample sorted through a 48-key sub-sample; 3M give
+    1,465 buckets, a 23,440-key sample and a 192-key sub-sample."""
+    db = datagen.make_db(n, 128, seed=n + parts)
+    idx = hc.hc_build(dev(db), partitions=parts)
+    oidx = O.build(db, curves=8, m=16, ell=parts)
+    assert_lists_equal(hc, idx, oidx)
+    idx.free()
+
+
+def test_oversize_bucket_goes_to_fallback(hc):
+    """30,000 copies of one row make a bucket of equal keys larger than a
+    block holds, and groups of 40 copies make runs longer than a warp sorts:
+    both are sorted by the fallback kernel by (key, low word, id)."""
+    rng = np.random.default_rng(5)
+    base = datagen.make_db(170_000, 128, seed=77)
+    dup = np.repeat(base[:1], 30_000, axis=0)
+    groups = np.repeat(base[1:101], 40, axis=0)
+    db = np.concatenate([base, dup, groups])[rng.permutation(170_000 + 30_000 + 4_000)]
+    db = np.ascontiguousarray(db)
+    idx = hc.hc_build(dev(db))
+    oidx = O.build(db, curves=8, m=16)
+    assert_lists_equal(hc, idx, oidx)
+    q = np.ascontiguousarray(np.concatenate([base[:5], db[:20]]))
+    rids, rdist = O.search(oidx, db, q, 10, 50)
+    gids, gdist = hc.hc_query(idx, dev(q), 10, 50)
+    sync()
+    assert np.array_equal(gids.cpu().numpy(), rids)
+    assert np.array_equal(gdist.cpu().numpy(), O.int32_dist(rdist))
+    idx.free()
+
+
+def test_equal_sample_keys_beyond_a_block(hc):
+    """Half of 2M rows equal: the sample then holds more equal keys than a
+    block sorts, so the sample's bucket hands the whole key range to one
+    list bucket, which the fallback sorts."""
+    rng = np.random.default_rng(9)
+    base = datagen.make_db(1_000_000, 128, seed=91)
+    db = np.concatenate([base, np.repeat(base[:1], 1_000_000, axis=0)])
+    db = np.ascontiguousarray(db[rng.permutation(len(db))])
+    idx = hc.hc_build(dev(db))
+    oidx = O.build(db, curves=8, m=16)
+    assert_lists_equal(hc, idx, oidx)
+    idx.free()
+
+
+def test_identical_rows_only(hc):
+    """Every row equal: every key of a list is equal and the lists are the
+    ids in order."""
+    db = np.repeat(datagen.make_db(1, 128, seed=3), 50_000, axis=0)
+    idx = hc.hc_build(dev(db), partitions=2)
+    oidx = O.build(db, curves=8, m=16, ell=2)
+    assert_lists_equal(hc, idx, oidx)
+    idx.free()
+
+
+def test_build_returns_without_waiting(hc):
+    """hc_build queues its work and returns: behind a kernel that keeps the
+    stream busy for about a second, the call comes back long before the
+    stream is idle, and the lists are then right."""
+    import torch
+    db = datagen.make_db(300_000, 128, seed=12)
+    tdb = dev(db)
+    hc.hc_build(tdb).free()          # load the kernels first
+    sync()
+    stream = torch.cuda.current_stream()
+    torch.cuda._sleep(2_000_000_000)   # ~1 s of clock cycles on the stream
+    t0 = time.perf_counter()
+    idx = hc.hc_build(tdb, stream=stream)
+    t_call = time.perf_counter() - t0
+    busy = not stream.query()
+    sync()
+    assert busy, "the stream went idle before the call returned"
+    assert t_call < 0.25, "hc_build took %.3f s on the host" % t_call
+    assert_lists_equal(hc, idx, O.build(db, curves=8, m=16))
+    idx.free()

@@ -70,6 +70,33 @@ def test_noalloc_matches_allocating_sort_twice(hc):
             assert np.array_equal(b[2].cpu().numpy().view(np.uint32)[x:y], ids[x:y][order])
 
 
+def test_noalloc_at_its_limits_allocates_nothing(hc):
+    """The largest problem within both limits -- 255 one-record segments and
+    one segment of the rest, 262,144 records in all -- needs nearly the whole
+    scratch array; it sorts like hc_sort_keys.  After a first call (which
+    loads the array on the device), a further call leaves the device's free
+    memory unchanged: the library allocated nothing."""
+    import torch
+    sizes = [1] * 255 + [262_144 - 255]
+    off, hi, lo, ids = random_records(4, sizes)
+    empty = torch.empty(0, dtype=torch.int64, device="cuda")
+    hc.hc_sort_keys_noalloc(empty, empty, empty.to(torch.int32), np.zeros(2, np.uint64), 128)
+    a = to_dev(hi, lo, ids)
+    b = to_dev(hi, lo, ids)
+    c = to_dev(hi, lo, ids)
+    hc.hc_sort_keys(*a, off, 128)
+    hc.hc_sort_keys_noalloc(*b, off, 128)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    hc.hc_sort_keys_noalloc(*c, off, 128)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    for t in (b, c):
+        assert np.array_equal(u64(a[0]), u64(t[0]))
+        assert np.array_equal(u64(a[1]), u64(t[1]))
+        assert np.array_equal(a[2].cpu().numpy(), t[2].cpu().numpy())
+
+
 def test_noalloc_rejects_problems_above_its_limit(hc):
     off, hi, lo, ids = random_records(3, [262_145])
     t = to_dev(hi, lo, ids)
