@@ -90,20 +90,18 @@ typedef struct {
 
 /*
  * hc_build -- Algorithm 1 on the GPU: for every partition and curve, the
- * extended-key of each row's projection, then a device sort of (key, id),
- * giving one list sorted by (key, id) per (partition, curve).  For
- * 16-coordinate curves the sort is a sample sort of the high key words
- * (buckets of about 2048 entries between splitters drawn from a sample,
- * each bucket sorted in shared memory; a tie of high words is broken by the
- * low words recomputed from the rows, then by id); shorter keys are radix-
- * sorted by every key byte.
+ * extended-key of each row's projection, then a stable device radix sort of
+ * (key, id), giving one list sorted by (key, id) per (partition, curve).  For
+ * 16-coordinate curves the top 56 bits of the key are radix-sorted and runs
+ * of equal 56-bit prefixes are then ordered by the whole key (the low word
+ * recomputed from the rows) and id; shorter keys are sorted by every byte.
  *   db_dev   n x d rows (uint8 or float32 per params->dtype), 16-byte aligned.
  *            NOT copied: the index keeps the pointer, so the caller keeps the
  *            buffer alive and unchanged until hc_free.
  *   out      receives the new index (owned by the library; free with hc_free).
  * The library allocates the index arrays (12 bytes per row and curve for
  * 16-coordinate curves, whose lists keep the high key word and the id; 20
- * bytes otherwise) and, during the call, stream-ordered scratch of about 27
+ * bytes otherwise) and, during the call, stream-ordered scratch of about 26
  * bytes per row and curve (33 when low words are kept); HC_ERR_OOM if that
  * fails.  All work is queued on cuda_stream and the call returns without
  * waiting on it; the index may be used by later work on the same stream (or

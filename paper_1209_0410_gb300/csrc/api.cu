@@ -173,28 +173,21 @@ int build_index(hc_index* x, cudaStream_t s) {
     std::vector<uint64_t> id_base(x->lists);
     for (uint32_t L = 0; L < x->lists; ++L)
         id_base[L] = partition_start(L / P.curves, P.n, parts);
-    // 16-coordinate keys: a sample sort of the high words, ties of the high
-    // word broken by low words recomputed from the rows.  Shorter keys: the
-    // radix sort by every key byte (the low words are stored).  Neither
-    // waits on the host.
+    // 16-coordinate keys: the top 7 bytes of the high words are radix-sorted,
+    // the last pass writing the final high words and ids, and runs of equal
+    // 56-bit prefixes are ordered by (high word, low word, id) on the device,
+    // the low words recomputed from the rows.  Shorter keys: every key byte
+    // is sorted (the low words are stored).  Neither waits on the host.
     SortProblem sp;
-    BucketSortProblem bp;
-    size_t sort_bytes;
-    if (keep_lo) {
-        sp.seg_off = x->list_off;
-        sp.seg_off_dev = x->list_off_dev;
-        sp.key_bits = 8 * P.dims_per_curve;
-        sp.allow_sync = false;
-        sp.out_hi = x->keys_hi;
-        sp.out_lo = x->keys_lo;
-        sp.out_ids = x->ids;
-        sort_bytes = sort_scratch_bytes(sp);
-    } else {
-        bp.seg_off = x->list_off;
-        bp.out_hi = x->keys_hi;
-        bp.out_ids = x->ids;
-        sort_bytes = bucket_sort_scratch_bytes(bp.seg_off);
-    }
+    sp.seg_off = x->list_off;
+    sp.seg_off_dev = x->list_off_dev;
+    sp.key_bits = 8 * P.dims_per_curve;
+    sp.allow_sync = false;
+    sp.hi_skip = keep_lo ? 0 : 1;
+    sp.out_hi = x->keys_hi;
+    sp.out_lo = x->keys_lo;
+    sp.out_ids = x->ids;
+    const size_t sort_bytes = sort_scratch_bytes(sp);
     const size_t key_bytes = ((sizeof(uint64_t) * (keep_lo ? 2 : 1) * total) + 255) & ~(size_t)255;
     const size_t base_bytes = (sizeof(uint64_t) * x->lists + 255) & ~(size_t)255;
     void* scratch = nullptr;
@@ -210,18 +203,12 @@ int build_index(hc_index* x, cudaStream_t s) {
     if (rc == HC_OK)
         rc = status_of(upload_small(id_base_dev, id_base.data(), sizeof(uint64_t) * x->lists, s));
     if (rc == HC_OK) {
-        if (keep_lo) {
-            sp.hi = hi0;
-            sp.lo = lo0;
-            sp.ids = nullptr;
-            sp.id_base_dev = id_base_dev;
-            rc = sort_segments(sp, sort_scratch, s);
-        } else {
-            bp.keys = hi0;
-            bp.id_base_dev = id_base_dev;
-            bp.rows = RowKeys{x->db, x->row_bytes, view_of(x).P};
-            rc = bucket_sort(bp, sort_scratch, s);
-        }
+        sp.hi = hi0;
+        sp.lo = lo0;
+        sp.ids = nullptr;
+        sp.id_base_dev = id_base_dev;
+        sp.rows = RowKeys{x->db, x->row_bytes, view_of(x).P};
+        rc = sort_segments(sp, sort_scratch, s);
     }
     const int frc = status_of(cudaFreeAsync(scratch, s));
     return rc ? rc : frc;

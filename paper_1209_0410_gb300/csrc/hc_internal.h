@@ -55,9 +55,11 @@ struct SortProblem {
     std::vector<uint64_t> seg_off;  // host, nseg+1 (grid sizes)
     const uint64_t* seg_off_dev;    // the same offsets on the device
     uint32_t key_bits;         // 1..128
-    // May the sort synchronise the stream once (to learn whether a run of
-    // equal high words is too long for the high-word-first path)?  With
-    // false, every digit is sorted and nothing waits on the device.
+    // With lo words (or gathered ids): may the sort synchronise the stream
+    // once (to learn whether a run of equal high words is too long for the
+    // high-word-first path)?  With false, every digit is sorted and nothing
+    // waits on the device.  Affine ids without lo words never wait: long
+    // runs are sorted on the device.
     bool allow_sync = false;
     // On that path, low digits of the high word left to the run fix-up (runs
     // of records whose other high-word bits are equal); 0 sorts every digit.
@@ -67,35 +69,16 @@ struct SortProblem {
     // lo == nullptr (high-word-first path with affine ids only): the low word
     // of record i of segment s is recomputed from row id_base[s] + i - seg
     // start on curve s % rows.P.curves, when a tie of the high words needs
-    // it; out_lo is not written.  A run of equal high-word prefixes too long
-    // for the fix-up then returns kSortNeedsLow (the caller supplies lo and
-    // sorts again).
+    // it; out_lo is not written.
     RowKeys rows{};
     uint64_t* out_hi;          // device, total records (distinct from sources)
     uint64_t* out_lo;
     uint32_t* out_ids;
 };
-constexpr int kSortNeedsLow = 2;
 // Scratch bytes the sort needs for this problem (queried before allocating).
 size_t sort_scratch_bytes(const SortProblem& p);
 // Enqueues the whole sort on s using the given scratch (>= sort_scratch_bytes).
 int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s);
-
-// Sample sort of high key words by segment (bucket_sort.cu), for indexes of
-// 16-coordinate curves whose ids are affine in the list position and whose
-// low words are recomputed from the rows: record i of segment s has id
-// id_base[s] + i, and the segments leave ordered by (high word, low word,
-// id).  Everything runs on the stream without a host wait.
-struct BucketSortProblem {
-    uint64_t* keys = nullptr;          // device, high words by segment; used as scratch
-    std::vector<uint64_t> seg_off;     // host, nseg+1
-    const uint64_t* id_base_dev = nullptr;   // device, nseg
-    RowKeys rows{};
-    uint64_t* out_hi = nullptr;        // device, total records
-    uint32_t* out_ids = nullptr;
-};
-size_t bucket_sort_scratch_bytes(const std::vector<uint64_t>& seg_off);
-int bucket_sort(const BucketSortProblem& p, void* scratch, cudaStream_t s);
 
 // Small host tables written to device memory by a kernel that takes them
 // as a by-value parameter, so that no pageable copy (and its implicit

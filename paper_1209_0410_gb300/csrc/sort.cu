@@ -10,13 +10,16 @@
 //   - at the end the low words and ids are gathered by the final positions.
 // Digits above key_bits are zero by contract and are skipped.
 //
-// When the caller may wait once on the stream (hc_build), the high-word-first
-// path sorts only the top bytes of the high word (hi_skip low bytes left out)
-// and a fix-up orders the short runs of equal prefixes by (high word, low
-// word, id).  For an index with affine ids and no stored low words the last
-// pass writes the final high words and ids and the fix-up works in place
-// (find_runs lists the run starts, sort_runs orders each run with one warp);
-// a run longer than 32 sends the caller back for a sort by every byte.
+// The high-word-first path sorts only the top bytes of the high word (hi_skip
+// low bytes left out) and a fix-up orders the short runs of equal prefixes by
+// (high word, low word, id).  For an index with affine ids and no stored low
+// words (hc_build) the last pass writes the final high words and ids and the
+// fix-up works in place and on the device alone: find_runs lists the run
+// starts, sort_runs orders each run of at most 32 records with one warp and
+// lists the longer ones, and long_run_kernel sorts those with one block each
+// through global memory.  Otherwise (low words stored, ids gathered) the
+// path is taken only when the caller may wait once on the stream: a run
+// longer than 32 then sends it back to sort by every byte.
 //
 // Per pass, three kernels, none of which waits on another block:
 //   hist    one 4096-record tile per block: digit counts -> counts[seg][digit][tile]
@@ -416,7 +419,8 @@ __global__ void __launch_bounds__(256) fixup_final_kernel(
 //              chunks of a warp loaded at once) and appends the position and
 //              segment of every run start to a list, one atomic per block;
 //   sort_runs  gives each listed run to one warp, one record per lane (at
-//              most kMaxRun = 32 records; a longer one sets *long_run):
+//              most kMaxRun = 32 records; a longer one is listed for
+//              long_run_kernel):
 //              lanes whose high words tie compute their low words, every lane
 //              counts the run's records below its own, and all lanes write
 //              after all have read.
@@ -503,7 +507,8 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
 __global__ void __launch_bounds__(256) sort_runs_kernel(
     uint64_t* hi, uint32_t* ids, int run_shift, RowKeys rows, const SegInfo* __restrict__ segs,
     const uint64_t* __restrict__ run_pos, const uint32_t* __restrict__ run_seg,
-    const unsigned long long* __restrict__ nruns, uint32_t* __restrict__ long_run) {
+    const unsigned long long* __restrict__ nruns, uint4* __restrict__ long_list,
+    uint32_t* __restrict__ long_count) {
     static_assert(kMaxRun == 32, "one run record per lane");
     const int lane = threadIdx.x & 31;
     const uint64_t n = *nruns;
@@ -524,7 +529,9 @@ __global__ void __launch_bounds__(256) sort_runs_kernel(
         const uint32_t inmask = __ballot_sync(0xffffffffu, in);
         const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
         if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == rkey) {
-            if (lane == 0) atomicOr(long_run, 1u);
+            if (lane == 0)
+                long_list[atomicAdd(long_count, 1u)] =
+                    make_uint4((uint32_t)rs, (uint32_t)(rs >> 32), seg, 0u);
             continue;
         }
         const bool mine = (uint32_t)lane < len;
@@ -550,6 +557,165 @@ __global__ void __launch_bounds__(256) sort_runs_kernel(
     }
 }
 
+// Runs of more than kMaxRun records with equal prefixes hi >> run_shift, as
+// listed by sort_runs: one block per run (grid-stride over the list; with an
+// empty list every block returns at once).  A run's records arrive in id
+// order; stable 8-bit passes over the bytes in which their low words (from
+// the rows), then the bits of their high words below run_shift, differ leave
+// them ordered by (high word, low word, id).  Scratch, the run's own stretch
+// of each: the low words in lo_buf, two permutations in pa_buf and pb_buf.
+constexpr int kRThreads = 1024;
+constexpr int kRWarps = kRThreads / 32;
+
+struct LongRunSmem {
+    uint32_t hist[256];
+    uint32_t wcnt[kRWarps][256];
+    uint32_t warp_sums[kRWarps];
+    uint64_t red[2][kRWarps];
+    unsigned long long end;
+};
+
+// byte `byte` of element i's low word (f = 0) or high word (f = 1)
+__device__ __forceinline__ uint32_t run_digit(int f, int byte, uint32_t i, const uint64_t* h,
+                                              const uint64_t* lo) {
+    const uint64_t x = f ? h[i] : lo[i];
+    return (uint32_t)(x >> (8 * byte)) & 0xFFu;
+}
+
+// Stable pass of one block over n elements: `in` (null: identity) is the
+// order so far, `out` receives the order by the digit.  Elements go in
+// chunks of one per thread; within a chunk a warp ranks its lanes by ballots
+// and the per-warp digit counts are scanned digit by digit over the warps.
+__device__ void long_run_pass(const uint32_t* in, uint32_t* out, uint32_t n, int f, int byte,
+                              const uint64_t* h, const uint64_t* lo, LongRunSmem& sm) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int i = t; i < 256; i += kRThreads) sm.hist[i] = 0;
+    for (int i = t; i < kRWarps * 256; i += kRThreads) (&sm.wcnt[0][0])[i] = 0;
+    __syncthreads();
+    for (uint32_t i = t; i < n; i += kRThreads)
+        atomicAdd(&sm.hist[run_digit(f, byte, in ? in[i] : i, h, lo)], 1u);
+    __syncthreads();
+    {
+        const uint32_t v = t < 256 ? sm.hist[t] : 0u;
+        const uint32_t ex = block_exclusive_scan<kRWarps>(v, sm.warp_sums);
+        if (t < 256) sm.hist[t] = ex;
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t c0 = 0; c0 < n; c0 += kRThreads) {
+        const uint32_t i = c0 + (uint32_t)t;
+        const bool valid = i < n;
+        const uint32_t r = valid ? (in ? in[i] : i) : 0u;
+        const uint32_t d = valid ? run_digit(f, byte, r, h, lo) : 0u;
+        const uint32_t peers = digit_peers(d) & __ballot_sync(0xffffffffu, valid);
+        if (valid && (peers & lt) == 0) sm.wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (t < 256) {
+            uint32_t run = sm.hist[t];
+            for (int w = 0; w < kRWarps; ++w) {
+                const uint32_t c = sm.wcnt[w][t];
+                sm.wcnt[w][t] = run;
+                run += c;
+            }
+            sm.hist[t] = run;
+        }
+        __syncthreads();
+        if (valid) out[sm.wcnt[warp][d] + __popc(peers & lt)] = r;
+        __syncthreads();
+        for (int j = t; j < kRWarps * 256; j += kRThreads) (&sm.wcnt[0][0])[j] = 0;
+        __syncthreads();
+    }
+}
+
+template <typename Op>
+__device__ __forceinline__ uint64_t block_reduce64(uint64_t v, uint64_t* red, Op op) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    uint64_t r = red[0];
+    for (int w = 1; w < kRWarps; ++w) r = op(r, red[w]);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kRThreads) long_run_kernel(
+    uint64_t* hi, uint32_t* ids, uint64_t* lo_buf, uint32_t* pa_buf, uint32_t* pb_buf,
+    int run_shift, RowKeys rows, const SegInfo* __restrict__ segs,
+    const uint4* __restrict__ long_list, const uint32_t* __restrict__ long_count) {
+    __shared__ LongRunSmem sm;
+    const int t = threadIdx.x;
+    const uint32_t total = *long_count;
+    for (uint32_t e = blockIdx.x; e < total; e += gridDim.x) {
+        const uint4 fe = long_list[e];
+        const uint64_t rs = ((uint64_t)fe.y << 32) | fe.x;
+        const uint32_t seg = fe.z;
+        const uint64_t seg_end = segs[seg].start + segs[seg].len;
+        const uint64_t pre = hi[rs] >> run_shift;
+        // the run ends at the first position after rs with another prefix
+        if (t == 0) sm.end = seg_end;
+        __syncthreads();
+        for (uint64_t c0 = rs + 1;; c0 += kRThreads) {
+            const uint64_t i = c0 + (uint64_t)t;
+            if (i < seg_end && (hi[i] >> run_shift) != pre) atomicMin(&sm.end, i);
+            __syncthreads();
+            const bool done = sm.end != seg_end || c0 + kRThreads >= seg_end;
+            __syncthreads();
+            if (done) break;
+        }
+        const uint32_t n = (uint32_t)(sm.end - rs);
+        uint64_t* h = hi + rs;
+        uint32_t* d = ids + rs;
+        uint64_t* lo = lo_buf + rs;
+        uint32_t* pa = pa_buf + rs;
+        uint32_t* pb = pb_buf + rs;
+        const uint32_t curve = seg % rows.P.curves;
+        uint64_t ol = 0, al = ~0ull, oh = 0, ah = ~0ull;
+        for (uint32_t i = t; i < n; i += kRThreads) {
+            const uint64_t l = row_key_lo(rows.db, rows.row_bytes, rows.P, d[i], curve);
+            lo[i] = l;
+            ol |= l;
+            al &= l;
+            oh |= h[i];
+            ah &= h[i];
+        }
+        auto bor = [](uint64_t x, uint64_t y) { return x | y; };
+        auto band = [](uint64_t x, uint64_t y) { return x & y; };
+        const uint64_t vary_l = block_reduce64(ol, sm.red[0], bor) &
+                                ~block_reduce64(al, sm.red[1], band);
+        const uint64_t vary_h = block_reduce64(oh, sm.red[0], bor) &
+                                ~block_reduce64(ah, sm.red[1], band);
+        const uint32_t* in = nullptr;
+        uint32_t* out = pa;
+        for (int f = 0; f < 2; ++f) {
+            const uint64_t vary = f ? vary_h : vary_l;
+            const int bytes = f ? run_shift / 8 : 8;
+            for (int byte = 0; byte < bytes; ++byte) {
+                if (((vary >> (8 * byte)) & 0xFFu) == 0) continue;
+                long_run_pass(in, out, n, f, byte, h, lo, sm);
+                in = out;
+                out = out == pa ? pb : pa;
+            }
+        }
+        if (in) {
+            // permute in place through the buffers no longer needed
+            uint32_t* dcopy = in == pa ? pb : pa;
+            for (uint32_t i = t; i < n; i += kRThreads) {
+                lo[i] = h[i];
+                dcopy[i] = d[i];
+            }
+            __syncthreads();
+            for (uint32_t i = t; i < n; i += kRThreads) {
+                const uint32_t r = in[i];
+                h[i] = lo[r];
+                d[i] = dcopy[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 uint32_t* pbuf_of(uint32_t* a, uint32_t* b, int which) { return which ? b : a; }
@@ -559,7 +725,7 @@ struct Layout {
     uint32_t nseg = 0, ntiles = 0;
     uint64_t ncounts = 0;
     size_t off_w = 0, off_pa = 0, off_pb = 0, off_counts = 0, off_totals = 0, off_segs = 0,
-           off_flag = 0, off_digits = 0, bytes = 0;
+           off_flag = 0, off_digits = 0, off_long = 0, bytes = 0;
 };
 
 Layout make_layout(const SortProblem& p) {
@@ -581,6 +747,8 @@ Layout make_layout(const SortProblem& p) {
     L.off_segs = o;    o = align_up(o + sizeof(SegInfo) * (L.nseg ? L.nseg : 1));
     L.off_flag = o;    o = align_up(o + 16);   // flag word; run count at +8
     L.off_digits = o;  o = align_up(o + L.total);
+    // runs longer than kMaxRun: at most total / (kMaxRun + 1) of them
+    L.off_long = o;    o = align_up(o + sizeof(uint4) * (L.total / (kMaxRun + 1) + 1));
     L.bytes = o;
     return L;
 }
@@ -659,14 +827,14 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     // following histogram (within one key word)
     uint8_t* dgt = reinterpret_cast<uint8_t*>(base + L.off_digits);
 
-    if (p.allow_sync && hi_passes > 0 && L.ntiles) {
+    // affine ids without low words: the last pass writes the final high
+    // words and ids, and only runs are fixed up in place, on the device
+    const bool in_place = p.lo == nullptr && p.id_base_dev != nullptr;
+    if ((p.allow_sync || in_place) && hi_passes > 0 && L.ntiles) {
         // sort by the high word's top bytes alone (skipping its lowest
         // hi_skip digits when more remain), then order runs of equal prefixes
         const int skip = (p.hi_skip > 0 && hi_passes > p.hi_skip) ? p.hi_skip : 0;
         const int npass = hi_passes - skip;
-        // affine ids without low words: the last pass writes the final high
-        // words and ids, and only runs are fixed up in place
-        const bool in_place = p.lo == nullptr && p.id_base_dev != nullptr;
         uint64_t* wb[2] = {wtmp, p.out_hi};
         // the last pass writes wtmp (or out_hi when in place)
         int wn = ((npass % 2 == 1) != in_place) ? 0 : 1;
@@ -691,7 +859,9 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             wn ^= 1;
             pn ^= 1;
         }
-        // the flag word, then (8 bytes on) the run count of the in-place fix-up
+        // the flag word, the count of long runs (4 bytes on), then (8 bytes
+        // on) the run count of the in-place fix-up
+        uint32_t* long_count = reinterpret_cast<uint32_t*>(base + L.off_flag + 4);
         unsigned long long* nruns = reinterpret_cast<unsigned long long*>(base + L.off_flag + 8);
         if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return HC_ERR_CUDA;
         if (in_place) {
@@ -700,11 +870,18 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             // most total / 2 runs (two records or more each) fit in either
             uint64_t* run_pos = reinterpret_cast<uint64_t*>(pa);
             uint32_t* run_seg = pb;
+            uint4* long_list = reinterpret_cast<uint4*>(base + L.off_long);
             find_runs_kernel<<<L.ntiles, kFindWarps * 32, 0, s>>>(p.out_hi, 8 * skip, L.nseg, segs,
                                                                 run_pos, run_seg, nruns);
             sort_runs_kernel<<<grid_stride_blocks(L.total / 64), 256, 0, s>>>(
-                p.out_hi, p.out_ids, 8 * skip, p.rows, segs, run_pos, run_seg, nruns, flag);
-            count_launches(1);
+                p.out_hi, p.out_ids, 8 * skip, p.rows, segs, run_pos, run_seg, nruns, long_list,
+                long_count);
+            // the word and position buffers are free now: scratch of the long runs
+            long_run_kernel<<<std::min<uint32_t>(L.ntiles, 152), kRThreads, 0, s>>>(
+                p.out_hi, p.out_ids, wtmp, pa, pb, 8 * skip, p.rows, segs, long_list, long_count);
+            count_launches(3);
+            if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
+            return HC_OK;
         } else {
             if (cw != wtmp) return HC_ERR_STATE;
             fixup_final_kernel<<<L.ntiles, 256, 0, s>>>(
@@ -721,9 +898,8 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
         if (!long_run) return HC_OK;
         // a run of equal high words longer than the fix-up handles: sort
         // again with every digit (the sources are untouched)
-        if (!p.lo) return kSortNeedsLow;
     }
-    if (!p.lo) return kSortNeedsLow;   // every digit needs the low words
+    if (!p.lo) return HC_ERR_STATE;   // every digit needs the low words
     // word buffers written in sequence: each lo pass, the hi gather, each hi
     // pass; alternate so that the last write lands in out_hi.
     const int writes = lo_passes + 1 + hi_passes;

@@ -1,13 +1,12 @@
-"""Algorithm 1's sorted lists from hc_build's sample sort, against the oracle.
+"""Algorithm 1's sorted lists from hc_build, against the oracle.
 
-Every list is cut into buckets of about 2048 entries by splitters taken from
-a sample of its keys (itself sorted through a smaller sub-sample), and every
-bucket is sorted in shared memory; buckets too large for that, or holding a
-run of more than 32 entries equal in their sorted bits, are sorted by a
-fallback kernel.  The cases below reach each of those paths at sizes the
-oracle builds in seconds, and the lists must equal the oracle's bit for bit
-(keys, low words recomputed from the rows, ids).  The last case checks that
-hc_build returns without waiting for its stream.
+hc_build radix-sorts the top 56 bits of every 16-coordinate key; runs of
+entries with equal 56-bit prefixes are then ordered by (key, low word, id)
+on the device: runs of up to 32 entries by one warp each, longer runs by one
+block each through global memory.  The cases below reach each of those paths
+at sizes the oracle builds in seconds, and the lists must equal the oracle's
+bit for bit (keys, low words recomputed from the rows, ids).  The last case
+checks that hc_build returns without waiting for its stream.
 """
 import time
 
@@ -50,10 +49,9 @@ def assert_lists_equal(hc, idx, oidx):
 
 
 @pytest.mark.parametrize("n,parts", [(600_000, 1), (900_000, 3), (3_000_000, 1)])
-def test_sampled_levels_bit_exact(hc, n, parts):
-    """Lists long enough for all three levels: 600k entries give 293 buckets
-    split by a 4,688-key sample sorted through a 48-key sub-sample; 3M give
-    1,465 buckets, a 23,440-key sample and a 192-key sub-sample."""
+def test_long_lists_bit_exact(hc, n, parts):
+    """Lists of 300k to 3M entries: many sort tiles per list, ragged last
+    tiles, and the short runs of equal 56-bit prefixes such lists hold."""
     db = datagen.make_db(n, 128, seed=n + parts)
     idx = hc.hc_build(dev(db), partitions=parts)
     oidx = O.build(db, curves=8, m=16, ell=parts)
@@ -61,10 +59,10 @@ def test_sampled_levels_bit_exact(hc, n, parts):
     idx.free()
 
 
-def test_oversize_bucket_goes_to_fallback(hc):
-    """30,000 copies of one row make a bucket of equal keys larger than a
-    block holds, and groups of 40 copies make runs longer than a warp sorts:
-    both are sorted by the fallback kernel by (key, low word, id)."""
+def test_long_runs_sorted_on_the_device(hc):
+    """30,000 copies of one row make a run of equal keys far longer than a
+    warp sorts, and groups of 40 copies make runs just beyond it: both are
+    ordered by one block each, by (key, low word, id)."""
     rng = np.random.default_rng(5)
     base = datagen.make_db(170_000, 128, seed=77)
     dup = np.repeat(base[:1], 30_000, axis=0)
@@ -83,10 +81,9 @@ def test_oversize_bucket_goes_to_fallback(hc):
     idx.free()
 
 
-def test_equal_sample_keys_beyond_a_block(hc):
-    """Half of 2M rows equal: the sample then holds more equal keys than a
-    block sorts, so the sample's bucket hands the whole key range to one
-    list bucket, which the fallback sorts."""
+def test_run_of_a_million_equal_keys(hc):
+    """Half of 2M rows equal: every list holds one run of a million equal
+    keys, ordered by id."""
     rng = np.random.default_rng(9)
     base = datagen.make_db(1_000_000, 128, seed=91)
     db = np.concatenate([base, np.repeat(base[:1], 1_000_000, axis=0)])
