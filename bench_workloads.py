@@ -265,67 +265,106 @@ def run_serve(a):
 
     per_req = 32
     arrivals = arrival_times(a.serve_seconds, seed=17, per_request=per_req)
-    srv = hc.Server([idx], 2 << 30, streams=4, max_batch_queries=8192, default_p=128)
+    srv = hc.Server([idx], 2 << 30, streams=4, max_batch_queries=8192, default_p=128,
+                    max_wait_us=200)
     srv.attach_predictor(0, mlp, margin, 1, 512)
-    tickets = [None] * len(arrivals)
-    done = []
 
-    def submitter():
-        start = time.perf_counter()
-        for i, ta in enumerate(arrivals):
-            while True:
-                now = time.perf_counter() - start
-                if now >= ta:
-                    break
-                if ta - now > 0.0005:
-                    time.sleep(ta - now - 0.0004)
-            s0 = (i * per_req) % (pool.shape[0] - per_req)
-            tickets[i] = srv.submit(0, pool[s0:s0 + per_req], 10, 0)
+    def open_loop(arr, p):
+        """Submits per_req-query requests at the given arrival times (seconds)
+        from one thread while another polls; returns latencies (s) and wall."""
+        tickets = [None] * len(arr)
+        done = []
 
-    def poller():
-        for i in range(len(arrivals)):
-            while tickets[i] is None:
-                time.sleep(0.0001)
-            r = None
-            while r is None:
-                r = srv.poll(tickets[i], 1_000_000, with_latency=True)
-            done.append((i, r[2], time.perf_counter()))
+        def submitter():
+            start = time.perf_counter()
+            for i, ta in enumerate(arr):
+                while True:
+                    now = time.perf_counter() - start
+                    if now >= ta:
+                        break
+                    if ta - now > 0.0005:
+                        time.sleep(ta - now - 0.0004)
+                s0 = (i * per_req) % (pool.shape[0] - per_req)
+                tickets[i] = srv.submit(0, pool[s0:s0 + per_req], 10, p)
 
-    wall0 = time.perf_counter()
-    ts = threading.Thread(target=submitter)
-    tp = threading.Thread(target=poller)
-    ts.start()
-    tp.start()
-    ts.join()
-    tp.join()
-    wall = time.perf_counter() - wall0
+        def poller():
+            for i in range(len(arr)):
+                while tickets[i] is None:
+                    time.sleep(0.0001)
+                r = None
+                while r is None:
+                    r = srv.poll(tickets[i], 1_000_000, with_latency=True)
+                done.append(r[2])
+
+        w0 = time.perf_counter()
+        ts = threading.Thread(target=submitter)
+        tp = threading.Thread(target=poller)
+        ts.start()
+        tp.start()
+        ts.join()
+        tp.join()
+        return np.array(done), time.perf_counter() - w0
+
+    lat_s, wall = open_loop(arrivals, 0)
     st = srv.stats()
+    lat = lat_s * 1e3
+    served = len(lat_s) * per_req
+
+    # latency against offered load: Poisson arrivals at fixed rates, one
+    # second each, learned depth and fixed p = 128
+    load = []
+    rng = np.random.default_rng(23)
+    for rate in (50_000, 200_000, 500_000, 1_000_000, 2_000_000):
+        arr = np.cumsum(rng.exponential(per_req / rate, size=int(rate / per_req * 1.2)))
+        arr = arr[arr < 1.0]
+        row = {"offered_qps": rate}
+        for name, p in (("learned", 0), ("fixed_p128", 128)):
+            l_s, w = open_loop(arr, p)
+            row[name] = {"served_qps": len(l_s) * per_req / w,
+                         "p50_ms": float(np.percentile(l_s, 50) * 1e3),
+                         "p99_ms": float(np.percentile(l_s, 99) * 1e3)}
+        load.append(row)
 
     # saturation: a closed loop keeps `outstanding` requests of sat_req queries
     # in the server for about two seconds (capacity rather than offered load)
+    def closed_loop(p, sat_req=4096, outstanding=16, seconds=2.0):
+        lat_c, nq_c, pending, i = [], 0, [], 0
+        t0c = time.perf_counter()
+        while True:
+            while len(pending) < outstanding and time.perf_counter() - t0c < seconds:
+                s0 = (i * sat_req) % (pool.shape[0] - sat_req)
+                pending.append(srv.submit(0, pool[s0:s0 + sat_req], 10, p))
+                i += 1
+            if not pending:
+                break
+            r = None
+            while r is None:
+                r = srv.poll(pending[0], 1_000_000, with_latency=True)
+            pending.pop(0)
+            lat_c.append(r[2])
+            nq_c += sat_req
+        return nq_c / (time.perf_counter() - t0c), np.array(lat_c) * 1e3
+
     sat_req, outstanding = 4096, 16
-    sat_lat, sat_q = [], 0
-    pending = []
-    t_sat0 = time.perf_counter()
-    i = 0
-    while True:
-        while len(pending) < outstanding and time.perf_counter() - t_sat0 < 2.0:
-            s0 = (i * sat_req) % (pool.shape[0] - sat_req)
-            pending.append(srv.submit(0, pool[s0:s0 + sat_req], 10, 0))
-            i += 1
-        if not pending:
-            break
-        r = None
-        while r is None:
-            r = srv.poll(pending[0], 1_000_000, with_latency=True)
-        pending.pop(0)
-        sat_lat.append(r[2])
-        sat_q += sat_req
-    sat_wall = time.perf_counter() - t_sat0
+    sat_qps, sat_lat = closed_loop(0)
+    sat_qps_fixed, sat_lat_fixed = closed_loop(128)
     srv.close()
-    sat_lat = np.array(sat_lat) * 1e3
-    lat = np.array([d[1] for d in done]) * 1e3
-    served = len(done) * per_req
+
+    # the plain method on the same index: one batch of 100k queries at fixed
+    # p = 128, answered in key order, timed on the device
+    qb = torch.from_numpy(np.ascontiguousarray(pool[:100_000])).cuda()
+    ob_ids = torch.empty((qb.shape[0], 10), dtype=torch.int32, device="cuda")
+    ob_dist = torch.empty((qb.shape[0], 10), dtype=torch.int32, device="cuda")
+    ws = torch.empty(hc.hc_query_ordered_workspace(qb.shape[0]), dtype=torch.uint8,
+                     device="cuda")
+    hc.hc_query_ordered(idx, qb, 10, 128, ob_ids, ob_dist, workspace=ws)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(5):
+        hc.hc_query_ordered(idx, qb, 10, 128, ob_ids, ob_dist, workspace=ws)
+    ev[1].record()
+    torch.cuda.synchronize()
+    plain_qps = qb.shape[0] / (ev[0].elapsed_time(ev[1]) / 5 / 1000.0)
     # recall of the served answers (learned depths) on a sample
     sample = torch.from_numpy(pool[:1000]).cuda()
     pd = mlp.predict_depths(idx, sample, margin, 1, 512)
@@ -350,11 +389,17 @@ def run_serve(a):
                       "recall_at_10": rec, "recall_at_10_fixed_p128": r128,
                       "server": {k: int(v) for k, v in st.items()},
                       "mean_batch_queries": st["queries_done"] / max(1, st["batches_done"]),
-                      "saturation": {"qps": sat_q / sat_wall, "request_queries": sat_req,
+                      "max_wait_us": 200,
+                      "latency_vs_offered_load": load,
+                      "saturation": {"qps": sat_qps, "request_queries": sat_req,
                                      "outstanding_requests": outstanding,
-                                     "seconds": sat_wall,
                                      "latency_ms": {"p50": float(np.percentile(sat_lat, 50)),
-                                                    "p99": float(np.percentile(sat_lat, 99))}},
+                                                    "p99": float(np.percentile(sat_lat, 99))},
+                                     "fixed_p128_qps": sat_qps_fixed,
+                                     "fixed_p128_latency_ms": {
+                                         "p50": float(np.percentile(sat_lat_fixed, 50)),
+                                         "p99": float(np.percentile(sat_lat_fixed, 99))}},
+                      "plain_fixed_p128_batch_qps": plain_qps,
                       "setup_s": setup_s}})
     mlp.free()
     return 0

@@ -433,9 +433,10 @@ HC_API void hc_mlp_free(hc_mlp* mlp);
  * budget.  The paper sends a GPU buffer of queued queries to the GPU when it
  * is full or when the GPU is idle (Sec. 6, Algorithm 3, without its CPU
  * branch here) and double-buffers the transfers (Sec. 5.2).  The server's
- * dispatcher thread dispatches a batch when no batch is running, or when the
- * queued queries fill a batch; up to `streams` batches run at once, so
- * requests that arrive while others are on the GPU overlap with them.  The
+ * dispatcher thread dispatches a batch when no batch is running, when the
+ * queued queries fill a batch, or when the oldest queued request has waited
+ * max_wait_us; up to `streams` batches run at once, so requests that arrive
+ * while others are on the GPU overlap with them.  The
  * device state of every in-flight request (queries, depths, results) lives in
  * an arena of exactly hbm_budget bytes allocated at creation: a request is
  * admitted into a batch only when its state fits, and one that cannot fit even
@@ -450,6 +451,9 @@ typedef struct {
     uint32_t max_batch_queries;  /* queries that fill a batch (default 16384) */
     uint32_t default_p;          /* depth used for requests submitted with p = 0
                                     (default 128) */
+    uint32_t max_wait_us;        /* latency bound: a batch also goes out, to a free
+                                    stream, once the oldest queued request has waited
+                                    this long (default 200; 0 = no bound) */
 } hc_serve_params;
 
 typedef struct {

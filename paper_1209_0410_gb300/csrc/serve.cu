@@ -5,7 +5,10 @@
 // it is full, or when the GPU is idle.  Without the CPU branch (there is no
 // CPU kNN here) that rule is the dispatcher below:
 //   - a batch is dispatched when no batch is running on the GPU, or when the
-//     queued queries fill a batch (max_batch_queries);
+//     queued queries fill a batch (max_batch_queries), or -- a latency bound
+//     the paper's rule does not have -- when the oldest queued request has
+//     waited max_wait_us, so that under load batches overlap on the GPU
+//     instead of queueing behind the one in flight;
 //   - several batches may run at once, one per stream ("slot"), so requests
 //     that arrive while others are on the GPU overlap with them;
 //   - all device state of in-flight requests (queries, per-query depths,
@@ -286,7 +289,8 @@ void dispatcher_loop(hc_server* S) {
         if (S->stop && S->queue.empty() && S->inflight.empty()) break;
 
         // DTAHE's flush rule without the CPU branch: dispatch when the GPU is
-        // idle, or when the queued queries fill a batch
+        // idle, or when the queued queries fill a batch; and when the oldest
+        // queued request has waited max_wait_us
         int slot = -1;
         for (size_t s = 0; s < S->slot_busy.size(); ++s)
             if (!S->slot_busy[s]) {
@@ -295,7 +299,10 @@ void dispatcher_loop(hc_server* S) {
             }
         const bool gpu_idle = S->inflight.empty();
         const bool full = S->queued_queries >= S->params.max_batch_queries;
-        if (!S->queue.empty() && slot >= 0 && (gpu_idle || full)) {
+        const bool waited = !S->queue.empty() && S->params.max_wait_us > 0 &&
+                            now_ns() - S->queue.front()->t_submit >=
+                                1000ull * S->params.max_wait_us;
+        if (!S->queue.empty() && slot >= 0 && (gpu_idle || full || waited)) {
             Batch* b = form_batch(S, slot);
             if (b) {
                 S->inflight.push_back(b);
@@ -350,7 +357,7 @@ HC_API int hc_serve_create_ex(hc_index* const* idx, uint32_t n_idx, uint64_t hbm
     if (!idx || n_idx < 1 || hbm_budget < 4096) return HC_ERR_ARG;
     for (uint32_t i = 0; i < n_idx; ++i)
         if (!idx[i]) return HC_ERR_ARG;
-    hc_serve_params P{4, 16384, 128};
+    hc_serve_params P{4, 16384, 128, 200};
     if (params) P = *params;
     if (P.streams < 1 || P.streams > 16 || P.max_batch_queries < 1 || P.default_p < 1 ||
         P.default_p > (1u << 30))

@@ -43,7 +43,7 @@ class _IndexInfo(ctypes.Structure):
 
 class _ServeParams(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32),
-                ("default_p", ctypes.c_uint32)]
+                ("default_p", ctypes.c_uint32), ("max_wait_us", ctypes.c_uint32)]
 
 
 class _ServeStats(ctypes.Structure):
@@ -435,10 +435,11 @@ def hc_debug_fail_alloc(after):
 class Server:
     """An hc_server: continuous batching over resident indexes (see hc.h)."""
 
-    def __init__(self, indexes, hbm_budget, streams=4, max_batch_queries=16384, default_p=128):
+    def __init__(self, indexes, hbm_budget, streams=4, max_batch_queries=16384, default_p=128,
+                 max_wait_us=200):
         self.indexes = list(indexes)      # keep them alive while serving
         arr = (_vp * len(self.indexes))(*[ix.handle for ix in self.indexes])
-        prm = _ServeParams(streams, max_batch_queries, default_p)
+        prm = _ServeParams(streams, max_batch_queries, default_p, max_wait_us)
         h = ctypes.c_void_p()
         _check(lib().hc_serve_create_ex(arr, len(self.indexes), hbm_budget, ctypes.byref(prm),
                                         ctypes.byref(h)), "hc_serve_create")

@@ -1,13 +1,19 @@
-"""Many indexes in one persistent launch (and its CUDA graph) against
-per-index hc_query calls: the same kernels' arithmetic, so every result must
-match bit for bit (uint8 and float32), whatever the warps per query, block
-configuration, batch sizes (including 0 and 1) or task order."""
+"""Many indexes in one persistent launch (and its CUDA graph), against the CPU
+oracle's Algorithm 2 on every job and against per-index hc_query calls.
+
+Against the oracle: uint8 ids and int32 distances bit for bit, float32
+distances within 1e-5 relative with id sets equal outside the tie band at
+the k-th distance, for every warps-per-query split (whose per-warp top-k
+lists are merged in shared memory), block configuration, k in {1, 10, 33,
+100}, d in {64, 128, 256} and batch sizes 0 to 1000.  Against hc_query: the
+same arithmetic, so bit for bit on both element types."""
 import json
 
 import numpy as np
 import pytest
 
-from helpers import dev
+from helpers import compare_f32, dev
+from oracle import oracle as O
 from paper_1209_0410_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
@@ -41,6 +47,57 @@ def jobs_data(hc):
         idx = hc.hc_build(dev(db), d // 16, 16)
         out.append((idx, dev(np.ascontiguousarray(q)), k, p, db))
     return out
+
+
+@pytest.fixture(scope="module")
+def oracle_results(jobs_data):
+    """Algorithm 2 of the CPU oracle for every job (ids, float64 distances)."""
+    out = []
+    for idx, q, k, p, db in jobs_data:
+        qn = q.cpu().numpy()
+        if qn.shape[0] == 0:
+            out.append(None)
+            continue
+        oidx = O.build(db, curves=db.shape[1] // 16, m=16)
+        out.append(O.search(oidx, db, qn, k, p))
+    return out
+
+
+def assert_matches_oracle(job, ref, db):
+    if ref is None:
+        assert job.ids.numel() == 0
+        return
+    rids, rdist = ref
+    gids, gdist = job.ids.cpu().numpy(), job.dist.cpu().numpy()
+    if db.dtype == np.uint8:
+        assert np.array_equal(gids, rids)
+        assert np.array_equal(gdist, O.int32_dist(rdist))
+    else:
+        assert compare_f32(gids, gdist, rids, rdist) == []
+
+
+@pytest.mark.parametrize("wpq", [1, 2, 4, 8])
+@pytest.mark.parametrize("cfg", [dict(warps_per_block=8, blocks_per_sm=2, tile=1),
+                                 dict(warps_per_block=16, blocks_per_sm=1, tile=3)])
+def test_multi_matches_oracle(hc, jobs_data, oracle_results, wpq, cfg):
+    import torch
+    jobs = [hc.MultiJob(idx, q, k, p, warps_per_query=wpq) for idx, q, k, p, _ in jobs_data]
+    hc.hc_query_multi(jobs, cfg)
+    torch.cuda.synchronize()
+    for j, ref, (_, _, _, _, db) in zip(jobs, oracle_results, jobs_data):
+        assert_matches_oracle(j, ref, db)
+
+
+def test_multi_graph_matches_oracle(hc, jobs_data, oracle_results):
+    import torch
+    jobs = [hc.MultiJob(idx, q, k, p, warps_per_query=4) for idx, q, k, p, _ in jobs_data]
+    plan = hc.MultiPlan(jobs, dict(warps_per_block=8, blocks_per_sm=2, tile=2, use_graph=True))
+    for _ in range(2):
+        plan.run()
+        torch.cuda.synchronize()
+        for j, ref, (_, _, _, _, db) in zip(jobs, oracle_results, jobs_data):
+            assert_matches_oracle(j, ref, db)
+    plan.free()
 
 
 def reference(hc, jobs_data):

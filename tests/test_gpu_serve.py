@@ -12,7 +12,8 @@ import time
 import numpy as np
 import pytest
 
-from helpers import dev
+from helpers import compare_f32, dev
+from oracle import oracle as O
 from paper_1209_0410_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
@@ -41,6 +42,33 @@ def indexes(hc):
     qb = datagen.make_queries(b, 3000, seed=72)
     qc = datagen.to_f32(datagen.make_queries(datagen.make_db(15000, 128, seed=63), 3000, seed=73))
     return [(ia, qa), (ib, qb), (ic, qc)]
+
+
+def test_served_results_match_oracle(hc, indexes):
+    """A sample of requests on all three indexes, served together, against
+    the CPU oracle's Algorithm 2: uint8 bit for bit, float32 within 1e-5
+    relative (ties at the k-th distance aside)."""
+    dbs = [datagen.make_db(30000, 128, seed=61), datagen.make_db(20000, 64, seed=62),
+           datagen.to_f32(datagen.make_db(15000, 128, seed=63))]
+    oidx = [O.build(db, curves=db.shape[1] // 16, m=16) for db in dbs]
+    specs = [(0, 0, 120, 10, 64), (1, 500, 77, 33, 30), (2, 1000, 90, 10, 50),
+             (0, 2000, 1, 1, 200), (2, 40, 64, 100, 16), (1, 2900, 100, 10, 0)]
+    srv = hc.hc_serve_create([ix for ix, _ in indexes], 128 << 20, streams=4,
+                             max_batch_queries=256, default_p=48)
+    try:
+        tickets = [srv.submit(i, indexes[i][1][s0:s0 + nq], k, p) for i, s0, nq, k, p in specs]
+        results = [srv.poll(t, 30_000_000) for t in tickets]
+    finally:
+        srv.close()
+    for (i, s0, nq, k, p), res in zip(specs, results):
+        assert res is not None
+        q = indexes[i][1][s0:s0 + nq]
+        rids, rdist = O.search(oidx[i], dbs[i], q, k, p if p else 48)
+        if dbs[i].dtype == np.uint8:
+            assert np.array_equal(res[0], rids)
+            assert np.array_equal(res[1], O.int32_dist(rdist))
+        else:
+            assert compare_f32(res[0], res[1], rids, rdist) == []
 
 
 def alone(hc, index, q, k, p):
@@ -116,6 +144,33 @@ def test_overlapping_batches_in_flight(hc, indexes):
     st = srv.stats()
     srv.close()
     assert st["max_inflight"] >= 2
+
+
+def test_latency_bound_overlaps_batches(hc, indexes):
+    """A small request that arrives while a long batch runs: with the latency
+    bound it goes out on a second stream after max_wait_us (two batches in
+    flight); without it (max_wait_us = 0) it waits for the GPU to go idle.
+    Either way its result equals hc_query alone."""
+    ix, q = indexes[0]
+    for wait_us, want_overlap in ((100, True), (0, False)):
+        srv = hc.hc_serve_create([ix], 512 << 20, streams=4, max_batch_queries=4096,
+                                 max_wait_us=wait_us)
+        try:
+            big = srv.submit(0, q[:3000], 10, 2000)
+            time.sleep(0.0002)
+            small = srv.submit(0, q[:64], 10, 64)
+            rs = srv.poll(small, 30_000_000)
+            rb = srv.poll(big, 30_000_000)
+            st = srv.stats()
+        finally:
+            srv.close()
+        assert rs is not None and rb is not None
+        rids, rdist = alone(hc, ix, q[:64], 10, 64)
+        assert np.array_equal(rs[0], rids) and np.array_equal(rs[1], rdist)
+        if want_overlap:
+            assert st["max_inflight"] >= 2
+        else:
+            assert st["max_inflight"] == 1
 
 
 def test_budget_admission(hc, indexes):

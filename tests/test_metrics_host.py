@@ -68,3 +68,22 @@ def test_fixed_recall_point_picks_smallest_depth_reaching_reference():
     sweep[1]["recall_at_10"] = 0.60
     assert bench.fixed_recall_point(sweep, 128)["p"] == 128
     assert bench.fixed_recall_point(sweep, 100) is None
+
+
+def test_build_bytes_counts_every_pass():
+    """The survey's build bytes (rows once, 20-byte records written, every
+    pass reading and writing every record) and the kernels' bytes, counted
+    here pass by pass for a small case."""
+    n, row, c = 1000, 128, 8
+    alg, ker = bench.build_bytes(n, row, c, passes=3)
+    r = c * n
+    assert alg == n * row + 20 * r + 3 * 40 * r
+    counts = 16 * 256 * r / 4096
+    keys = n * row + 8 * r
+    p1 = 8 * r + counts + 8 * r + 13 * r
+    p2 = 1 * r + counts + 12 * r + 13 * r
+    p3 = 1 * r + counts + 12 * r + 12 * r
+    assert ker == pytest.approx(keys + p1 + p2 + p3 + 8 * r)
+    # the headline workload: about 17.8 GB moved per build
+    _, k10 = bench.build_bytes(10_000_000, 128, 8)
+    assert 17.0e9 < k10 < 18.5e9
