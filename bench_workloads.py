@@ -5,15 +5,19 @@ uneven   64 independent indexes (N log-uniform in [10k, 2M], d in {64, 128,
          log-uniform in [1, 4096], k in {1, 10, 100}, p = 64: one persistent
          launch replayed from a CUDA graph (autotuned) against one hc_query
          launch per index.
-learned  N = 10M uint8, depth predictor trained on seeded queries (labels:
-         minimal p reproducing the p = 512 top-10), evaluated on held-out
-         queries: recall@10 (exact kNN on a sample), agreement with p = 512,
-         queries/s of learned against fixed depths at matched recall.
+learned  N = 10M uint8, depth predictor trained on the device on seeded
+         queries with two label targets (minimal p reproducing the p = 512
+         top-10, and the p = 128 top-10), evaluated on held-out queries:
+         recall@10 (exact kNN on a sample), agreement with p = 512, queries/s
+         of learned against fixed depths at matched recall.
 serve    N = 50M uint8 resident, Poisson arrivals whose rate follows seeded
          on/off bursts times a sinusoid between 10k and 500k queries/s, k = 10,
          requests with p = 0 (learned depth, fixed-depth fallback), HBM-budget
-         admission: p50/p99 latency and sustained queries/s; then a closed loop
-         of 4096-query requests for the server's capacity.
+         admission, a 200 us latency bound on batching: p50/p99 latency and
+         sustained queries/s; latency against offered load (fixed-rate
+         Poisson phases, learned and fixed depth); a closed loop of 4096-query
+         requests for the server's capacity; the plain fixed-depth batch
+         throughput on the same index.
 partitions
          partitioned Hypercurves on one GPU (Sec. 4): N = 10M uint8 split into
          ell in {1, 2, 4, 8, 16, 32} in-HBM partitions, sequential depth
@@ -141,10 +145,6 @@ def run_learned(a):
     tqh = torch.from_numpy(qh).cuda()
     idx = hc.hc_build(tdb, 8, 16)
     torch.cuda.synchronize()
-    t0 = time.time()
-    mlp, labels, losses = learned.fit(idx, tqt, k=10, p_max=512, epochs=8, batch=4096)
-    torch.cuda.synchronize()
-    train_s = time.time() - t0
     rs = min(2000, a.heldout_queries)
     _, tdist = hc.hc_bruteforce(tdb, tqh[:rs], 10)
     ref512, _ = hc.hc_query(idx, tqh, 10, 512)
@@ -166,39 +166,51 @@ def run_learned(a):
         fixed.append({"p": p, "ms": ms, "qps": a.heldout_queries / (ms / 1e3),
                       "recall_at_10": learned.recall_at_10(ids[:rs], dist[:rs], tdist),
                       "agreement_p512": learned.agreement(ids, ref512)})
-    r128 = [f for f in fixed if f["p"] == 128][0]["recall_at_10"]
-    curve = []
-    chosen = None
-    for m in [x / 4.0 for x in range(-16, 9)]:
-        def run(m=m):
-            pd = mlp.predict_depths(idx, tqh, m, 1, 512)
-            return hc.hc_query_depths(idx, tqh, 10, pd) + (pd,)
-        (ids, dist, pd), ms = timed(run)
-        row = {"margin": m, "mean_p": float(pd.double().mean().item()), "ms": ms,
-               "qps": a.heldout_queries / (ms / 1e3),
-               "recall_at_10": learned.recall_at_10(ids[:rs], dist[:rs], tdist),
-               "agreement_p512": learned.agreement(ids, ref512)}
-        curve.append(row)
-        if chosen is None and row["recall_at_10"] >= r128:
-            chosen = row
     base = [f for f in fixed if f["p"] == 128][0]
-    value = chosen["qps"] if chosen else None
+    r128 = base["recall_at_10"]
+    # two label targets: the large depth of the configuration (p = 512) and
+    # the operating point itself (p = 128)
+    targets = {}
+    for p_max in (512, 128):
+        t0 = time.time()
+        mlp, labels, losses = learned.fit(idx, tqt, k=10, p_max=p_max, epochs=8, batch=4096)
+        torch.cuda.synchronize()
+        train_s = time.time() - t0
+        curve, chosen = [], None
+        for m in [x / 4.0 for x in range(-16, 13)]:
+            def run(m=m):
+                pd = mlp.predict_depths(idx, tqh, m, 1, 512)
+                return hc.hc_query_depths(idx, tqh, 10, pd) + (pd,)
+            (ids, dist, pd), ms = timed(run)
+            row = {"margin": m, "mean_p": float(pd.double().mean().item()), "ms": ms,
+                   "qps": a.heldout_queries / (ms / 1e3),
+                   "recall_at_10": learned.recall_at_10(ids[:rs], dist[:rs], tdist),
+                   "agreement_p512": learned.agreement(ids, ref512)}
+            curve.append(row)
+            if chosen is None and row["recall_at_10"] >= r128:
+                chosen = row
+        targets["p_max_%d" % p_max] = {
+            "labels": "minimal p reproducing the p=%d top-10" % p_max,
+            "label_mean": float(labels.double().mean().item()), "train_s": train_s,
+            "loss_per_epoch": losses, "learned_at_matched_recall": chosen,
+            "speedup_vs_fixed_p128": (chosen["qps"] / base["qps"]) if chosen else None,
+            "learned_sweep": curve}
+        mlp.free()
+    best = max((t for t in targets.values() if t["learned_at_matched_recall"]),
+               key=lambda t: t["learned_at_matched_recall"]["qps"], default=None)
+    chosen = best["learned_at_matched_recall"] if best else None
     _line({"metric": "queries/s at recall@10 >= plain p=128, learned probe depth, 10M x 128 "
-                     "uint8", "value": value, "unit": "queries/s", "n_gpus": 1,
-           "steps": 3, "warmup": 1, "ms_per_step": chosen["ms"] if chosen else None,
+                     "uint8", "value": chosen["qps"] if chosen else None, "unit": "queries/s",
+           "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": chosen["ms"] if chosen else None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
            "data": "synthetic: seeded 64-cluster Gaussian mixture; train seed 4, held-out seed 5",
-           "config": {"workload": "learned depth: N=%d, MLP 32-64-64-1 (FP32 Adam training, BF16 "
-                                  "inference), %d train / %d held-out queries, labels = minimal "
-                                  "p reproducing the p=512 top-10"
+           "config": {"workload": "learned depth: N=%d, MLP 32-64-64-1 (FP32 Adam training on "
+                                  "the device, BF16 inference), %d train / %d held-out queries, "
+                                  "labels = minimal p reproducing the p=512 or the p=128 top-10"
                                   % (n, a.train_queries, a.heldout_queries),
-                      "train_s": train_s, "loss_per_epoch": losses,
-                      "label_mean": float(labels.double().mean().item()),
-                      "fixed_p128": base, "learned_at_matched_recall": chosen,
-                      "speedup_vs_fixed_p128": (chosen["qps"] / base["qps"]) if chosen else None,
-                      "fixed_sweep": fixed, "learned_sweep": curve,
+                      "fixed_p128": base, "value_from": best["labels"] if best else None,
+                      "label_targets": targets, "fixed_sweep": fixed,
                       "recall_sample_queries": rs}})
-    mlp.free()
     return 0
 
 

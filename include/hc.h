@@ -411,6 +411,24 @@ HC_API int hc_mlp_gradients(hc_mlp* mlp, const float* x_dev, const float* t_dev,
  * learning rate lr on one batch; loss_host as above. */
 HC_API int hc_mlp_train_step(hc_mlp* mlp, const float* x_dev, const float* t_dev, uint32_t n,
                              float lr, float* loss_host, void* cuda_stream);
+/*
+ * hc_mlp_fit -- trains the MLP on n samples, every step on the device:
+ * regression targets t = log2(max(label, 1)) of the depth labels; input
+ * normalisation mu = mean and isd = 1 / max(sd, 1e-3) of every feature
+ * column (unbiased sd), replacing the MLP's; then `epochs` passes, each over
+ * a fresh order of the samples (random 32-bit keys from SplitMix64 of
+ * (seed, epoch, sample), radix-sorted), in whole minibatches of `batch`
+ * samples (the remainder of an epoch is left out) gathered into contiguous
+ * buffers, one Adam step (hc_mlp_train_step) per minibatch at rate lr.
+ * losses_host[epochs] receives, per epoch, the mean training loss over every
+ * 50th minibatch.  feat_dev: n x in float; labels_dev: n uint32.  Set the
+ * initial parameters first (hc_mlp_set_params).  Allocates about
+ * 50 n + 4 batch (in + 1) bytes of scratch on cuda_stream and returns when
+ * the training has finished.  HC_ERR_ARG if batch > max_batch or n < batch.
+ */
+HC_API int hc_mlp_fit(hc_mlp* mlp, const float* feat_dev, const uint32_t* labels_dev, uint32_t n,
+                      uint32_t epochs, uint32_t batch, float lr, uint64_t seed, float* losses_host,
+                      void* cuda_stream);
 /* hc_mlp_forward -- y for n samples; bf16 = 0: FP32 throughout; bf16 = 1:
  * inputs of every layer and weights rounded to bfloat16, FP32 accumulation
  * (the inference arithmetic of hc_mlp_predict_depths). */

@@ -101,3 +101,49 @@ def forward_bf16(theta, mu, isd, X, n_in, h1, h2):
     a1 = to_bf16(np.maximum(xn @ to_bf16(P["W1"]) + P["b1"].astype(np.float32), 0.0))
     a2 = to_bf16(np.maximum(a1 @ to_bf16(P["W2"]) + P["b2"].astype(np.float32), 0.0))
     return a2 @ to_bf16(P["W3"]) + np.float32(P["b3"])
+
+
+def _fma32(a, b, c):
+    """a * b + c rounded once to float32 for float32 a, b, c: the product is
+    exact in float64 (24 + 24 significant bits); the float64 sum can round
+    once before the float32 rounding, which differs from a true fused
+    multiply-add only when that sum is inexact and lands on a float32 tie."""
+    return (np.asarray(a, np.float64) * np.asarray(b, np.float64)
+            + np.asarray(c, np.float64)).astype(np.float32)
+
+
+def forward_bf16_gpu_order(theta, mu, isd, X, n_in, h1, h2, lanes=32):
+    """Inference with every layer's inputs and the weights rounded to
+    bfloat16 and float32 sums taken in a fixed order: each hidden unit's sum
+    as a chain of fused multiply-adds over its inputs in index order, the
+    bias added after the chain, ReLU, then rounding to bfloat16; the output
+    as per-lane chains (lane l takes units l, l + lanes, ...) combined by a
+    butterfly of float32 additions (strides 16, 8, 4, 2, 1), plus the bias."""
+    P = unpack(np.asarray(theta, np.float64), n_in, h1, h2)
+    f32 = np.float32
+    W1 = to_bf16(P["W1"]).astype(f32)
+    W2 = to_bf16(P["W2"]).astype(f32)
+    W3 = to_bf16(P["W3"]).astype(f32)
+    b1 = np.asarray(P["b1"], f32)
+    b2 = np.asarray(P["b2"], f32)
+    b3 = f32(P["b3"])
+    X = np.asarray(X, f32)
+    xn = to_bf16((X - np.asarray(mu, f32)) * np.asarray(isd, f32)).astype(f32)
+    n = X.shape[0]
+    a = np.zeros((n, h1), f32)
+    for i in range(n_in):
+        a = _fma32(xn[:, i:i + 1], W1[i][None, :], a)
+    hid1 = to_bf16(np.maximum(a + b1, f32(0))).astype(f32)
+    a = np.zeros((n, h2), f32)
+    for i in range(h1):
+        a = _fma32(hid1[:, i:i + 1], W2[i][None, :], a)
+    hid2 = to_bf16(np.maximum(a + b2, f32(0))).astype(f32)
+    part = np.zeros((n, lanes), f32)
+    for j in range(h2):
+        part[:, j % lanes] = _fma32(hid2[:, j], W3[j], part[:, j % lanes])
+    lane = np.arange(lanes)
+    o = lanes // 2
+    while o >= 1:
+        part = (part + part[:, lane ^ o]).astype(f32)
+        o //= 2
+    return (part[:, 0] + b3).astype(f32)

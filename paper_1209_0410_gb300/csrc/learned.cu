@@ -558,6 +558,81 @@ int features_ok(const hc_index* idx) {
     return HC_OK;
 }
 
+// -------------------------------------------------------------- training
+// regression target of a depth label: log2(max(label, 1))
+__global__ void fit_targets_kernel(const uint32_t* __restrict__ labels, uint32_t n,
+                                   float* __restrict__ t) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) t[i] = log2f((float)(labels[i] > 1u ? labels[i] : 1u));
+}
+
+// One block per feature column: mean, then the unbiased standard deviation
+// about it (two passes, float64 sums); mu = mean, isd = 1 / max(sd, 1e-3).
+__global__ void __launch_bounds__(256) fit_stats_kernel(const float* __restrict__ x, uint32_t n,
+                                                        uint32_t in, float* __restrict__ mu,
+                                                        float* __restrict__ isd) {
+    __shared__ double red[8];
+    __shared__ double mean_s;
+    const uint32_t c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc = 0.0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) acc += (double)x[(size_t)i * in + c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        mean_s = t / (double)n;
+    }
+    __syncthreads();
+    const double mean = mean_s;
+    acc = 0.0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double d = (double)x[(size_t)i * in + c] - mean;
+        acc += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        const double sd = n > 1 ? sqrt(t / (double)(n - 1)) : 0.0;
+        mu[c] = (float)mean;
+        isd[c] = (float)(1.0 / (sd > 1e-3 ? sd : 1e-3));
+    }
+}
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) of a counter
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// random 32-bit sort keys of epoch e: the order of the samples in that epoch
+__global__ void fit_keys_kernel(uint64_t seed, uint32_t epoch, uint32_t n,
+                                uint64_t* __restrict__ keys) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        keys[i] = splitmix64(seed ^ ((uint64_t)epoch << 40) ^ (uint64_t)i) >> 32;
+}
+
+// minibatch j of an epoch: rows perm[b0 .. b0 + b) of x and t, made contiguous
+__global__ void fit_gather_kernel(const float* __restrict__ x, const float* __restrict__ t,
+                                  const uint32_t* __restrict__ perm, uint32_t b0, uint32_t b,
+                                  uint32_t in, float* __restrict__ xb, float* __restrict__ tb) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b * in) return;
+    const uint32_t j = k / in, c = k % in;
+    const uint32_t r = perm[b0 + j];
+    xb[k] = x[(size_t)r * in + c];
+    if (c == 0) tb[j] = t[r];
+}
+
 }  // namespace
 
 // predictor launch used by the serving loop (serve.cu)
@@ -737,10 +812,12 @@ HC_API int hc_mlp_gradients(hc_mlp* M, const float* x_dev, const float* t_dev, u
     return HC_OK;
 }
 
-HC_API int hc_mlp_train_step(hc_mlp* M, const float* x_dev, const float* t_dev, uint32_t n,
-                             float lr, float* loss_host, void* cuda_stream) {
-    if (!M || n < 1 || n > M->max_batch || !(lr > 0.f)) return HC_ERR_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+}  // extern "C"
+
+namespace {
+// forward, backward and one Adam step (beta 0.9 / 0.999, eps 1e-8) on a batch
+int train_step(hc_mlp* M, const float* x_dev, const float* t_dev, uint32_t n, float lr,
+               cudaStream_t s) {
     if (int rc = forward_backward(M, x_dev, t_dev, n, s, true)) return rc;
     M->steps += 1;
     const double b1 = 0.9, b2 = 0.999;
@@ -751,12 +828,109 @@ HC_API int hc_mlp_train_step(hc_mlp* M, const float* x_dev, const float* t_dev, 
                                                         c1, c2);
     count_launches(1);
     M->bf_stale = true;
-    if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? HC_OK : HC_ERR_CUDA;
+}
+}  // namespace
+
+extern "C" {
+
+HC_API int hc_mlp_train_step(hc_mlp* M, const float* x_dev, const float* t_dev, uint32_t n,
+                             float lr, float* loss_host, void* cuda_stream) {
+    if (!M || n < 1 || n > M->max_batch || !(lr > 0.f)) return HC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (int rc = train_step(M, x_dev, t_dev, n, lr, s)) return rc;
     if (loss_host) {
         if (cudaMemcpyAsync(loss_host, M->loss, sizeof(float), cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return HC_ERR_CUDA;
+    }
+    return HC_OK;
+}
+
+HC_API int hc_mlp_fit(hc_mlp* M, const float* feat_dev, const uint32_t* labels_dev, uint32_t n,
+                      uint32_t epochs, uint32_t batch, float lr, uint64_t seed, float* losses_host,
+                      void* cuda_stream) {
+    if (!M || batch < 1 || batch > M->max_batch || n < batch || epochs < 1 || !(lr > 0.f) ||
+        !losses_host || !dev_ptr(feat_dev) || !dev_ptr(labels_dev))
+        return HC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const Layout L = layout_of(M->in, M->h1, M->h2);
+    const uint32_t nbatch = n / batch;              // whole minibatches per epoch
+    const uint32_t every = 50;                      // minibatches between recorded losses
+    const uint32_t logs = (nbatch + every - 1) / every;
+    // scratch: targets | sort keys | sorted keys (two) | permutation | batch | losses | sort
+    SortProblem sp;
+    sp.seg_off = {0, (uint64_t)n};
+    sp.key_bits = 32;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_t = 0, o_keys = al(4ull * n), o_sh = o_keys + al(8ull * n),
+                 o_sl = o_sh + al(8ull * n), o_perm = o_sl + al(8ull * n),
+                 o_seg = o_perm + al(4ull * n), o_xb = o_seg + 256,
+                 o_tb = o_xb + al(4ull * batch * M->in), o_log = o_tb + al(4ull * batch),
+                 o_sort = o_log + al(4ull * logs * epochs), bytes = o_sort + sort_scratch_bytes(sp);
+    if (alloc_should_fail()) return HC_ERR_OOM;
+    char* buf = nullptr;
+    if (cudaMallocAsync((void**)&buf, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return HC_ERR_OOM;
+    }
+    float* t = reinterpret_cast<float*>(buf + o_t);
+    uint64_t* keys = reinterpret_cast<uint64_t*>(buf + o_keys);
+    uint32_t* perm = reinterpret_cast<uint32_t*>(buf + o_perm);
+    uint64_t* seg = reinterpret_cast<uint64_t*>(buf + o_seg);   // seg_off[2], id_base[1]
+    float* xb = reinterpret_cast<float*>(buf + o_xb);
+    float* tb = reinterpret_cast<float*>(buf + o_tb);
+    float* lg = reinterpret_cast<float*>(buf + o_log);
+    int rc = HC_OK;
+    fit_targets_kernel<<<(n + 255) / 256, 256, 0, s>>>(labels_dev, n, t);
+    fit_stats_kernel<<<M->in, 256, 0, s>>>(feat_dev, n, M->in, M->params + L.mu,
+                                           M->params + L.isd);
+    count_launches(2);
+    const uint64_t small[3] = {0, (uint64_t)n, 0};
+    if (upload_small(seg, small, sizeof(small), s) != cudaSuccess) rc = HC_ERR_CUDA;
+    sp.seg_off_dev = seg;
+    sp.hi = keys;   // carried along; only the 32 key bits in the low word are compared
+    sp.lo = keys;
+    sp.ids = nullptr;
+    sp.id_base_dev = seg + 2;   // ids = positions: the sorted ids are the permutation
+    sp.out_hi = reinterpret_cast<uint64_t*>(buf + o_sh);
+    sp.out_lo = reinterpret_cast<uint64_t*>(buf + o_sl);
+    sp.out_ids = perm;
+    std::vector<float> host_log((size_t)logs * epochs, 0.f);
+    for (uint32_t e = 0; !rc && e < epochs; ++e) {
+        fit_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(seed, e, n, keys);
+        count_launches(1);
+        if (cudaGetLastError() != cudaSuccess || (rc = sort_segments(sp, buf + o_sort, s))) {
+            if (!rc) rc = HC_ERR_CUDA;
+            break;
+        }
+        for (uint32_t j = 0; !rc && j < nbatch; ++j) {
+            const uint32_t cnt = batch * M->in;
+            fit_gather_kernel<<<(cnt + 255) / 256, 256, 0, s>>>(feat_dev, t, perm, j * batch, batch,
+                                                                M->in, xb, tb);
+            count_launches(1);
+            rc = train_step(M, xb, tb, batch, lr, s);
+            if (!rc && j % every == 0 &&
+                cudaMemcpyAsync(lg + (size_t)e * logs + j / every, M->loss, sizeof(float),
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                rc = HC_ERR_CUDA;
+        }
+    }
+    if (!rc && (cudaMemcpyAsync(host_log.data(), lg, sizeof(float) * host_log.size(),
+                                cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess))
+        rc = HC_ERR_CUDA;
+    cudaFreeAsync(buf, s);
+    cudaStreamSynchronize(s);
+    if (rc) {
+        cudaGetLastError();
+        return rc;
+    }
+    for (uint32_t e = 0; e < epochs; ++e) {
+        double sum = 0.0;
+        for (uint32_t j = 0; j < logs; ++j) sum += host_log[(size_t)e * logs + j];
+        losses_host[e] = (float)(sum / logs);
     }
     return HC_OK;
 }

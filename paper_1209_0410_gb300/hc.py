@@ -135,6 +135,7 @@ def lib():
                                      _vp]
         L.hc_launch_count.argtypes = []
         L.hc_launch_count.restype = ctypes.c_uint64
+        L.hc_mlp_fit.argtypes = [_vp, _vp, _vp, _u32, _u32, _u32, ctypes.c_float, _u64, _vp, _vp]
         L.hc_debug_fail_alloc.argtypes = [ctypes.c_long]
         L.hc_debug_fail_alloc.restype = None
         _LIB = L
@@ -575,6 +576,17 @@ class MLP:
                                        ctypes.byref(loss) if want_loss else None,
                                        _stream(stream)), "hc_mlp_train_step")
         return loss.value if want_loss else None
+
+    def fit(self, feats, labels, epochs, batch, lr, seed=0, stream=None):
+        """hc_mlp_fit: trains on (n, in) features and n depth labels on the
+        device; returns the mean loss per epoch."""
+        n = feats.shape[0]
+        losses = np.zeros(epochs, np.float32)
+        _check(lib().hc_mlp_fit(self.handle, _dev(feats, "feats"),
+                                _dev(labels.contiguous(), "labels"), n,
+                                epochs, batch, lr, seed, losses.ctypes.data_as(_vp),
+                                _stream(stream)), "hc_mlp_fit")
+        return [float(x) for x in losses]
 
     def forward(self, x, bf16=False, stream=None):
         y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)

@@ -1,9 +1,11 @@
 """Training and evaluation driver of the learned probe depth.
 
-Every arithmetic step runs in libhc kernels (labels: hc_probe_labels through
-the query kernel; features: hc_features; forward/backward/Adam:
-hc_mlp_train_step; inference: hc_mlp_predict_depths).  This module only
-orders the calls and moves minibatches (torch indexing on the device).
+Every arithmetic step runs in libhc kernels: labels (hc_probe_labels, through
+the query kernel), features (hc_features), training (hc_mlp_fit: targets,
+normalisation statistics, the per-epoch order of the samples, minibatch
+gathers and Adam steps, all on the device) and inference
+(hc_mlp_predict_depths).  This module only orders the calls; the initial
+weights are drawn on the host like any other seeded input.
 """
 import numpy as np
 import torch
@@ -20,11 +22,6 @@ def he_init(seed, n_in, h1, h2):
     return np.concatenate(parts).astype(np.float32)
 
 
-def depth_targets(labels):
-    """Regression target log2(max(p_min, 1))."""
-    return torch.log2(labels.clamp(min=1).to(torch.float32))
-
-
 def fit(index, q_train, k=10, p_max=512, epochs=12, batch=2048, lr=2e-3, seed=0,
         h1=64, h2=64, stream=None):
     """Labels, features and an Adam-trained MLP for one index.
@@ -33,28 +30,11 @@ def fit(index, q_train, k=10, p_max=512, epochs=12, batch=2048, lr=2e-3, seed=0,
     epoch."""
     labels = hc.hc_probe_labels(index, q_train, k, p_max, stream=stream)
     feats = hc.hc_features(index, q_train, stream=stream)
-    target = depth_targets(labels)
-    mu = feats.mean(dim=0)
-    sd = feats.std(dim=0).clamp(min=1e-3)
-    mlp = hc.MLP(feats.shape[1], h1, h2, max_batch=batch)
-    mlp.set_params(he_init(seed, feats.shape[1], h1, h2), mu.cpu().numpy(),
-                   (1.0 / sd).cpu().numpy())
-    gen = torch.Generator(device=q_train.device)
-    gen.manual_seed(seed)
-    n = feats.shape[0]
-    losses = []
-    for _ in range(epochs):
-        perm = torch.randperm(n, device=q_train.device, generator=gen)
-        tot, cnt = 0.0, 0
-        for i in range(0, n - batch + 1, batch):
-            sel = perm[i:i + batch]
-            want = (i // batch) % 50 == 0
-            l = mlp.train_step(feats[sel].contiguous(), target[sel].contiguous(), lr,
-                               want_loss=want, stream=stream)
-            if want:
-                tot += l
-                cnt += 1
-        losses.append(tot / max(cnt, 1))
+    n_in = feats.shape[1]
+    mlp = hc.MLP(n_in, h1, h2, max_batch=batch)
+    mlp.set_params(he_init(seed, n_in, h1, h2), np.zeros(n_in, np.float32),
+                   np.ones(n_in, np.float32))
+    losses = mlp.fit(feats, labels, epochs, batch, lr, seed=seed, stream=stream)
     return mlp, labels, losses
 
 

@@ -131,3 +131,58 @@ def test_depth_labels_minimal_and_sufficient():
         if lab[i] > 0:
             below, _ = O.search(index, db, q[i:i + 1], k, int(lab[i]) - 1)
             assert not np.array_equal(below[0], ref[i])
+
+
+def test_gpu_order_forward_exact_on_representable_values():
+    """With small-integer weights and inputs every partial sum is an integer
+    below 2^24, exact in float32 and in float64 alike, so the GPU-order
+    forward equals the float64-sum bfloat16 forward (same rounding points)
+    bit for bit; and the first hidden layer (sums below 256, exact in
+    bfloat16) matches the plain float64 forward's."""
+    rng = np.random.default_rng(3)
+    n_in, h1, h2 = 12, 40, 36
+    theta = rng.integers(-3, 4, M.count(n_in, h1, h2)).astype(np.float64)
+    X = rng.integers(0, 8, (50, n_in)).astype(np.float64)
+    mu, isd = np.zeros(n_in), np.ones(n_in)
+    yb = M.forward_bf16(theta, mu, isd, X, n_in, h1, h2)
+    yg = M.forward_bf16_gpu_order(theta, mu, isd, X, n_in, h1, h2)
+    assert np.array_equal(yg.astype(np.float64), yb)
+    _, (_, _, a1, _, _) = M.forward(theta, mu, isd, X, n_in, h1, h2)
+    assert np.abs(a1).max() < 256
+
+
+def test_gpu_order_forward_close_to_float64_forward():
+    """On random data the GPU-order forward stays within bfloat16 resolution
+    of the float64 bfloat16 forward (which rounds the same values)."""
+    rng = np.random.default_rng(4)
+    n_in, h1, h2 = 32, 64, 64
+    theta = M.init(5, n_in, h1, h2)
+    X = rng.normal(0, 1, (400, n_in))
+    mu, isd = np.zeros(n_in), np.ones(n_in)
+    yg = M.forward_bf16_gpu_order(theta, mu, isd, X, n_in, h1, h2).astype(np.float64)
+    yb = M.forward_bf16(theta, mu, isd, X, n_in, h1, h2)
+    scale = 1 + np.abs(yb).max()
+    assert np.median(np.abs(yg - yb)) <= 1e-4 * scale
+    assert np.max(np.abs(yg - yb)) <= 3e-2 * scale
+
+
+def test_gpu_order_output_butterfly():
+    """The output sum: 64 units on 32 lanes, lane l holding units l and
+    l + 32, combined by the butterfly; with one unit non-zero per lane the
+    result is their float32 sum in the butterfly's order."""
+    n_in, h1, h2 = 1, 1, 64
+    theta = np.zeros(M.count(n_in, h1, h2))
+    P = M.unpack(theta.copy(), n_in, h1, h2)
+    P["W1"][:] = 1.0
+    P["W2"][:] = 1.0
+    P["W3"][:] = 2.0 ** -np.arange(64)          # exact in bfloat16
+    theta = M.pack(P, n_in, h1, h2)
+    y = M.forward_bf16_gpu_order(theta, np.zeros(1), np.ones(1), np.ones((1, 1)), n_in, h1, h2)
+    lanes = np.zeros(32, np.float32)
+    for j in range(64):
+        lanes[j % 32] = np.float32(lanes[j % 32] + np.float32(2.0 ** -j))
+    o = 16
+    while o >= 1:
+        lanes = (lanes + lanes[np.arange(32) ^ o]).astype(np.float32)
+        o //= 2
+    assert y[0] == lanes[0]
