@@ -245,9 +245,10 @@ def build_bytes(n, row_bytes, curves, passes=BUILD_PASSES):
 
 def algorithmic_query_bytes(hc, idx, q_dev, p, k, row_bytes):
     """Bytes the method itself must move for one query launch (per query:
-    window ids 4 B + window rows, the global binary-search probes beyond 12
-    cached levels at 8 B (the high key word; the low word is needed only on
-    the rare ties), the query row and k (id, distance) results)."""
+    window ids 4 B + window rows, every probe of the binary search in every
+    list at 8 B (the high key word; the low word is needed only on the rare
+    ties; the kernel stages no levels in shared memory), the query row and k
+    (id, distance) results)."""
     import torch
     pos = hc.hc_query_positions(idx, q_dev)
     _, off = hc.hc_index_describe(idx)
@@ -256,7 +257,7 @@ def algorithmic_query_bytes(hc, idx, q_dev, p, k, row_bytes):
     hi = torch.minimum(pos + p, n_list.unsqueeze(0))
     windows = int((hi - lo).clamp(min=0).sum().item())
     nq, lists = pos.shape
-    lg = sum(max(0, int(n).bit_length() - 12) for n in (off[1:] - off[:-1]).tolist())
+    lg = sum(int(n).bit_length() for n in (off[1:] - off[:-1]).tolist())
     return windows * (row_bytes + 4) + nq * (lg * 8 + row_bytes + k * 8), windows
 
 

@@ -347,13 +347,16 @@ __device__ __forceinline__ uint64_t staged_candidates(const uint8_t* sbuf, uint3
     return r < cnt ? ((uint64_t)dist_bits(dsum) << 32) | cid : kEmpty;
 }
 
-template <bool F32, int LPR, int KR>
+// S ring stages: the copies of S - 1 steps are in flight while one is
+// reduced, and the ids of the step after those are loaded.
+template <bool F32, int LPR, int KR, int S = 2>
 __device__ __forceinline__ void search_lists_staged(const IndexView& ix, const uint8_t* qrow,
                                                     uint32_t depth, uint32_t k, uint32_t L0,
                                                     uint32_t Lstep, uint32_t* pos_w,
                                                     uint32_t* win_pre, uint8_t* ring,
                                                     WarpTopK<KR>& top, int lane,
                                                     const int64_t* pos_in = nullptr) {
+    static_assert(S >= 2, "one step reduced while another is in flight");
     if (pos_in) {
         for (uint32_t L = L0 + (uint32_t)lane * Lstep; L < ix.lists; L += 32 * Lstep)
             pos_w[L] = (uint32_t)__ldg(pos_in + L);
@@ -372,28 +375,37 @@ __device__ __forceinline__ void search_lists_staged(const IndexView& ix, const u
     const uint32_t total = pack_windows(ix, depth, L0, Lstep, pos_w, win_at, win_pre, lane);
     const uint32_t steps = (total + 31) / 32;
     if (steps == 0) return;
-    // step A = 0 copied, step B = 1 ids loaded
-    uint32_t aid = packed_ids(ix, win_at, win_pre, nm, total, 0, lane);
-    issue_step(db, row_bytes, ring_s, aid, min(32u, total), lane);
-    cp_async_commit();
-    uint32_t bid = steps > 1 ? packed_ids(ix, win_at, win_pre, nm, total, 1, lane) : 0u;
-    uint32_t st = 0;
-    for (uint32_t a = 0; a < steps; ++a) {
-        if (a + 1 < steps)
-            issue_step(db, row_bytes, ring_s + (st ^ 1u) * stage_bytes, bid,
-                       min(32u, total - 32 * (a + 1)), lane);
+    // ids[j]: this lane's id of step a + j; steps a .. a + S - 2 are in flight
+    uint32_t ids[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+        ids[j] = (uint32_t)j < steps ? packed_ids(ix, win_at, win_pre, nm, total, j, lane) : 0u;
+#pragma unroll
+    for (int j = 0; j < S - 1; ++j) {
+        if ((uint32_t)j < steps)
+            issue_step(db, row_bytes, ring_s + (uint32_t)j * stage_bytes, ids[j],
+                       min(32u, total - 32 * (uint32_t)j), lane);
         cp_async_commit();
-        const uint32_t cid = a + 2 < steps ? packed_ids(ix, win_at, win_pre, nm, total, a + 2, lane)
+    }
+    uint32_t st = 0;   // stage of step a
+    for (uint32_t a = 0; a < steps; ++a) {
+        const uint32_t sn = st == 0 ? S - 1 : st - 1;   // stage of step a + S - 1
+        if (a + S - 1 < steps)
+            issue_step(db, row_bytes, ring_s + sn * stage_bytes, ids[S - 1],
+                       min(32u, total - 32 * (a + S - 1)), lane);
+        cp_async_commit();
+        const uint32_t nid = a + S < steps ? packed_ids(ix, win_at, win_pre, nm, total, a + S, lane)
                                            : 0u;
-        cp_async_wait<1>();   // step a has landed
+        cp_async_wait<S - 1>();   // step a has landed
         __syncwarp();
-        top.offer(staged_candidates<F32, LPR>(ring + st * stage_bytes, row_bytes, qv0, aid,
+        top.offer(staged_candidates<F32, LPR>(ring + st * stage_bytes, row_bytes, qv0, ids[0],
                                               min(32u, total - 32 * a), lane),
                   k, lane);
-        __syncwarp();         // every lane is done with stage st before it is refilled
-        aid = bid;
-        bid = cid;
-        st ^= 1u;
+        __syncwarp();             // every lane is done with stage st before it is refilled
+#pragma unroll
+        for (int j = 0; j < S - 1; ++j) ids[j] = ids[j + 1];
+        ids[S - 1] = nid;
+        st = st + 1 == S ? 0u : st + 1;
     }
     cp_async_wait<0>();
 }

@@ -36,6 +36,7 @@ namespace hc {
 namespace {
 
 constexpr int kQWarps = 8;
+constexpr int kStages = 2;   // ring stages per warp (deeper rings measured slower)
 
 struct QueryArgs {
     IndexView ix;
@@ -73,8 +74,8 @@ __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kerne
         // after the positions: kQWarps x lists window prefixes, then the rings
         uint32_t* s_pre = s_pos + kQWarps * ix.lists;
         uint8_t* ring = reinterpret_cast<uint8_t*>(s_pre + kQWarps * ix.lists) +
-                        (size_t)warp * 64 * ix.row_bytes;
-        search_lists_staged<F32, LPR, KR>(
+                        (size_t)warp * kStages * 32 * ix.row_bytes;
+        search_lists_staged<F32, LPR, KR, kStages>(
             ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, s_pre + warp * ix.lists, ring,
             top, lane, a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
     } else {
@@ -129,7 +130,7 @@ struct QueryLaunch {
         const size_t pos_bytes = sizeof(uint32_t) * kQWarps * a.ix.lists;
         // rows of at most 128 bytes (all rows of 4 or 8 lanes) are staged
         if constexpr (LPR <= 8) {
-            const size_t smem = 2 * pos_bytes + (size_t)kQWarps * 64 * a.ix.row_bytes;
+            const size_t smem = 2 * pos_bytes + (size_t)kQWarps * kStages * 32 * a.ix.row_bytes;
             return go<true>(a, smem, s);
         } else {
             return go<false>(a, pos_bytes, s);

@@ -39,8 +39,9 @@ def test_agreement_is_exact_topk_equality():
 
 
 def test_algorithmic_query_bytes_formula():
-    """Window rows and ids, the binary-search probes beyond 12 cached levels
-    (8 bytes each), the query row and the k results, from given positions."""
+    """Window rows and ids, every binary-search probe (8 bytes each; a list
+    of n entries takes ceil(log2(n + 1)) of them), the query row and the k
+    results, from given positions."""
     import types
     import numpy as np
     # two lists of 10 and 5000 entries; two queries
@@ -52,7 +53,7 @@ def test_algorithmic_query_bytes_formula():
     qbytes, windows = bench.algorithmic_query_bytes(fake, None, None, p, k, row)
     # windows: list 0 [0, 7) = 7 and [6, 10) = 4; list 1 [3996, 4004) and [96, 104) = 8 each
     assert windows == 7 + 4 + 8 + 8
-    probes = max(0, 10 .bit_length() - 12) + max(0, 5000 .bit_length() - 12)   # 0 + 1
+    probes = 4 + 13   # ceil(log2(11)) + ceil(log2(5001))
     assert qbytes == windows * (row + 4) + 2 * (probes * 8 + row + k * 8)
 
 
