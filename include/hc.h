@@ -63,7 +63,10 @@ typedef enum {
     HC_ERR_BUDGET = -4,         /* admission refused: over the HBM budget */
     HC_ERR_TIMEOUT = -5,        /* a host-side wait ran out of time */
     HC_ERR_DEVICE_STATUS = -6,  /* a kernel reported an error status */
-    HC_ERR_STATE = -7           /* object used in the wrong state (e.g. an unknown ticket) */
+    HC_ERR_STATE = -7,          /* object used in the wrong state (e.g. an unknown ticket) */
+    HC_ERR_IO = -8,             /* a file could not be opened, read or written */
+    HC_ERR_FORMAT = -9          /* a file is not an index file of this library, is damaged,
+                                   or does not index the database it is loaded over */
 } hc_status;
 
 typedef enum { HC_U8 = 0, HC_F32 = 1 } hc_dtype;
@@ -541,7 +544,95 @@ HC_API int hc_serve_stats_get(hc_server* srv, hc_serve_stats* out);
  * the server (uncollected results are dropped).  NULL is ok. */
 HC_API void hc_serve_destroy(hc_server* srv);
 
+/* --------------------------------------------------------- index files */
+
+/*
+ * hc_save -- writes an index to the file `path`: its build parameters, list
+ * offsets, and every list's sorted high key words, stored low key words
+ * (curves of fewer than 16 coordinates) and ids, i.e. the output of
+ * Algorithm 1.  The database rows are NOT written: hc_load takes them again.
+ * No counterpart in the paper, which rebuilds its index from the database.
+ *   idx          an index (hc_build, hc_build_host or hc_load); unchanged.
+ *   path         file name; written as path + ".tmp", then renamed over path,
+ *                so a reader never sees a half-written file.
+ *   cuda_stream  waited for first (the index may still be building on it);
+ *                the lists are then copied to the host through a 32 MB buffer.
+ * Layout (little-endian, each section a multiple of 8 bytes): an 80-byte
+ * header ("HCURVIDX", u32 version 1, u32 byte-order mark 0x01020304, u64 n,
+ * u32 d, curves, dims_per_curve, bits, dtype, partitions, lists, row_bytes,
+ * flags (bit 0: low words stored, bit 1: dim map stored), u32 0, u64 total
+ * entries), u64 list_off[lists + 1], u32 dim_map[curves * dims_per_curve]
+ * (flag bit 1, zero-padded), u64 keys_hi[total], u64 keys_lo[total] (flag
+ * bit 0), u32 ids[total] (zero-padded), then a u64 checksum of every 64-bit
+ * word before it.  About 12 bytes per row and curve (20 with low words).
+ * Returns HC_ERR_ARG for a null index or path, HC_ERR_IO when the file cannot
+ * be written (the temporary file is removed), HC_ERR_CUDA if a copy fails.
+ * Synchronous; safe while other threads query the same index.
+ */
+HC_API int hc_save(const hc_index* idx, const char* path, void* cuda_stream);
+
+/*
+ * hc_load -- an index from a file hc_save wrote, over the database it was
+ * built from.
+ *   path         the file.
+ *   db_dev       the n x d rows the index was built from (device memory,
+ *                16-byte aligned).  NOT copied: as with hc_build, the index
+ *                keeps the pointer and the caller keeps the rows alive and
+ *                unchanged until hc_free.
+ *   cuda_stream  the lists are uploaded on it; the call returns once they are
+ *                on the device and checked.
+ *   out          receives the index (free with hc_free).  It answers every
+ *                query exactly as the index that was saved.
+ * Nothing in the file is trusted.  Checked on the host before any device
+ * work: the header (magic, version, byte order, parameters valid as for
+ * hc_build), the list offsets against the layout hc_build makes for those
+ * parameters, and the file size.  Checked while the lists stream in: each
+ * list holds every row of its partition exactly once, high key words do not
+ * decrease along a list, and the checksum agrees.  Checked last on the
+ * device: the keys of up to 4096 entries per list, spread over the list and
+ * recomputed from db_dev's rows, equal the stored keys.  Returns HC_ERR_ARG
+ * for a null path or out, or a db_dev that is not 16-byte aligned device
+ * memory (checked after the header); HC_ERR_IO when the file cannot be
+ * opened or read; HC_ERR_FORMAT when any check fails; HC_ERR_OOM /
+ * HC_ERR_CUDA.  On an error nothing is allocated and *out is NULL.
+ */
+HC_API int hc_load(const char* path, const void* db_dev, void* cuda_stream, hc_index** out);
+
 /* ------------------------------------------------------------ testing */
+
+/*
+ * hc_check_status -- the bounds checks of the checked build.  The library
+ * also builds as libhc_check.so (every translation unit compiled with
+ * -DHC_CHECK): there, each checked device access first tests its index; an
+ * index out of range is counted, the first one is recorded and the access
+ * is skipped (a row id is replaced by row 0, a write is dropped), and every
+ * stream-ordered library buffer is followed by a 256-byte guard whose bytes
+ * are checked on the device before the buffer is freed and here for the
+ * buffers still alive.  Checked sites (hc_check_report.site):
+ *   1 key pass: a row's slot in its list      2 radix scatter: a destination
+ *   3 run fix-up: the run lists               4 run fix-up: a place in a run
+ *   5 long-run pass: an output place           6 lower_bound: a probed entry
+ *   7 a window's end against its list          8 a window entry index
+ *   9 a row id against the database rows     10 a query against the batch
+ *  11 persistent launch: a query of a job     12 persistent launch: lists
+ *  13 a guard byte overwritten (index = offset in the guard, bound 0)
+ * No counterpart in the paper: it stands in for a memory checker.
+ *   out    receives the report; violations counts every refused access (and
+ *          overwritten guard byte) since the last reset, site / index / bound
+ *          describe the first (index >= bound).  In the normal build
+ *          enabled = 0 and the rest is zero.
+ *   reset  nonzero: clear the device records after reading them.
+ * Waits for the whole device first (checked build only).  HC_ERR_ARG if out
+ * is NULL, HC_ERR_CUDA if a read fails.
+ */
+typedef struct {
+    uint32_t enabled;      /* 1 in libhc_check.so, 0 in libhc.so */
+    uint32_t site;         /* check site of the first violation, 0 = none */
+    uint64_t violations;   /* refused accesses and overwritten guard bytes */
+    uint64_t index;        /* the first violation's index ... */
+    uint64_t bound;        /* ... and the bound it broke */
+} hc_check_report;
+HC_API int hc_check_status(hc_check_report* out, int reset);
 
 /* hc_launch_count -- number of CUDA kernel launches the library has issued
  * since it was loaded (all entry points, all devices).  No counterpart in the

@@ -1,6 +1,8 @@
 """In-tree build of the native parts.
 
 libhc.so     : the CUDA library behind include/hc.h (nvcc, sm_103a only)
+libhc_check.so: the same sources with -DHC_CHECK (device bounds checks and
+               buffer guards, read back by hc_check_status)
 libhcgen.so  : the seeded input generator (plain C, gcc)
 
 Translation units compile in parallel into _build/ and link in place next to
@@ -52,28 +54,46 @@ def _run(cmd):
     return r.stdout
 
 
-def build_hc(force=False, verbose=False, extra_flags=()):
-    """Compile every csrc/*.cu for sm_103a and link libhc.so."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+HC_CHECK_LIB = os.path.join(PKG, "libhc_check.so")
+VARIANTS = {"normal": (HC_LIB, BUILD_DIR, []),
+            "check": (HC_CHECK_LIB, os.path.join(BUILD_DIR, "check"), ["-DHC_CHECK"])}
+
+
+def build_hc(force=False, verbose=False, extra_flags=(), variants=("normal",)):
+    """Compile every csrc/*.cu for sm_103a and link libhc.so (and, when
+    asked, libhc_check.so), all translation units of all variants in one
+    parallel pool.  Returns the path of the first variant's library."""
     sources = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
     headers = _headers()
     nvcc = _nvcc()
-    objs, jobs = [], []
-    for src in sources:
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        if force or _stale(obj, [src] + headers):
-            jobs.append([nvcc] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", src, "-o", obj])
+    plan, jobs = [], []
+    for v in variants:
+        lib, bdir, flags = VARIANTS[v]
+        os.makedirs(bdir, exist_ok=True)
+        objs = []
+        for src in sources:
+            obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+            objs.append(obj)
+            if force or _stale(obj, [src] + headers):
+                jobs.append([nvcc] + ARCH + NVCC_FLAGS + flags + list(extra_flags) +
+                            ["-c", src, "-o", obj])
+        plan.append((lib, objs))
     if jobs:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             for out in ex.map(_run, jobs):
                 if verbose and out.strip():
                     sys.stdout.write(out)
-    if force or jobs or _stale(HC_LIB, objs):
-        tmp = HC_LIB + ".tmp%d" % os.getpid()
-        _run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
-        os.replace(tmp, HC_LIB)
-    return HC_LIB
+    for lib, objs in plan:
+        if force or jobs or _stale(lib, objs):
+            tmp = lib + ".tmp%d" % os.getpid()
+            _run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
+            os.replace(tmp, lib)
+    return plan[0][0]
+
+
+def build_hc_check(force=False, verbose=False):
+    """libhc_check.so alone."""
+    return build_hc(force=force, verbose=verbose, variants=("check",))
 
 
 def build_datagen(force=False):
@@ -88,4 +108,4 @@ def build_datagen(force=False):
 
 if __name__ == "__main__":
     build_datagen(force="--force" in sys.argv)
-    print(build_hc(force="--force" in sys.argv, verbose=True))
+    print(build_hc(force="--force" in sys.argv, verbose=True, variants=("normal", "check")))

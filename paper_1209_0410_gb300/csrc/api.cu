@@ -2,10 +2,13 @@
 // around the kernels of keys.cu (K1), sort.cu (K2) and query.cu (K3..K6).
 #include <atomic>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "hc_index.h"
+#include "hc_trace.h"
 
 using namespace hc;
 
@@ -33,7 +36,7 @@ bool injected_failure() {
 
 bool hc::alloc_should_fail() { return injected_failure(); }
 
-namespace {
+namespace hc {
 
 int status_of(cudaError_t e) {
     if (e == cudaSuccess) return HC_OK;
@@ -44,6 +47,23 @@ int status_of(cudaError_t e) {
     return HC_ERR_CUDA;
 }
 
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// true when p is device memory of the current device (or managed)
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace hc
+
+namespace {
+
 int dev_alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (injected_failure()) return HC_ERR_OOM;
@@ -51,11 +71,35 @@ int dev_alloc(void** p, size_t bytes) {
     return status_of(cudaMalloc(p, bytes));
 }
 
+#ifdef HC_CHECK
+// Checked build: every stream-ordered buffer is followed by a guard of
+// kGuardBytes bytes of kGuardByte, checked on the device before the buffer is
+// freed and on the host by hc_check_status.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+std::mutex g_guard_mu;
+std::unordered_map<void*, size_t> g_guards;   // buffer -> bytes before its guard
+
+__global__ void guard_check_kernel(const unsigned char* g, uint32_t n) {
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+        if (g[i] != kGuardByte) hc::check_index(kSitePad, i, 0);
+}
+#endif
+
 int dev_alloc_async(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (injected_failure()) return HC_ERR_OOM;
     if (bytes == 0) bytes = 16;
+#ifdef HC_CHECK
+    if (int rc = status_of(cudaMallocAsync(p, bytes + kGuardBytes, s))) return rc;
+    {
+        std::lock_guard<std::mutex> g(g_guard_mu);
+        g_guards[*p] = bytes;
+    }
+    return status_of(cudaMemsetAsync(static_cast<char*>(*p) + bytes, kGuardByte, kGuardBytes, s));
+#else
     return status_of(cudaMallocAsync(p, bytes, s));
+#endif
 }
 
 void keep_pool_memory() {
@@ -70,19 +114,6 @@ void keep_pool_memory() {
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     cudaGetLastError();
-}
-
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-
-// true when p is device memory of the current device (or managed)
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 uint32_t row_bytes_of(hc_dtype t, uint32_t d) { return t == HC_F32 ? d * 4u : d; }
@@ -113,11 +144,43 @@ int check_params(const hc_build_params* p) {
 // stream order, so build/free cycles reuse pool memory without device syncs.
 // By default on the legacy stream, which waits for the work of every blocking
 // stream (safe whatever stream used the index); hc_free_async names the stream.
-void pool_free(void* p, cudaStream_t s = cudaStreamLegacy) {
-    if (p) cudaFreeAsync(p, s);
+cudaError_t pool_free(void* p, cudaStream_t s = cudaStreamLegacy) {
+    if (!p) return cudaSuccess;
+#ifdef HC_CHECK
+    size_t body = 0;
+    {
+        std::lock_guard<std::mutex> g(g_guard_mu);
+        auto it = g_guards.find(p);
+        if (it != g_guards.end()) {
+            body = it->second;
+            g_guards.erase(it);
+        }
+    }
+    if (body) {
+        guard_check_kernel<<<1, 256, 0, s>>>(static_cast<const unsigned char*>(p) + body,
+                                             (uint32_t)kGuardBytes);
+        count_launches(1);
+    }
+#endif
+    return cudaFreeAsync(p, s);
 }
 
-void destroy(hc_index* x, cudaStream_t s = cudaStreamLegacy) {
+}  // namespace
+
+namespace hc {
+
+static std::mutex g_readers_mu;
+static std::vector<CheckReader>& check_readers() {
+    static std::vector<CheckReader> v;
+    return v;
+}
+
+void register_check_reader(CheckReader r) {
+    std::lock_guard<std::mutex> g(g_readers_mu);
+    check_readers().push_back(r);
+}
+
+void index_destroy(hc_index* x, cudaStream_t s) {
     if (!x) return;
     pool_free(x->dim_map_dev, s);
     pool_free(x->db_owned, s);
@@ -131,8 +194,7 @@ void destroy(hc_index* x, cudaStream_t s = cudaStreamLegacy) {
     delete x;
 }
 
-// Algorithm 1 for an index whose params, db and dim_map are set.
-int build_index(hc_index* x, cudaStream_t s) {
+void index_layout(hc_index* x) {
     const hc_build_params& P = x->params;
     const uint32_t parts = P.partitions;
     x->lists = parts * P.curves;
@@ -143,6 +205,11 @@ int build_index(hc_index* x, cudaStream_t s) {
         const uint64_t len = partition_start(j + 1, P.n, parts) - partition_start(j, P.n, parts);
         x->list_off[L + 1] = x->list_off[L] + len;
     }
+}
+
+bool index_keeps_lo(const hc_build_params& P) { return P.dims_per_curve < 16; }
+
+int index_alloc(hc_index* x, cudaStream_t s) {
     const uint64_t total = x->list_off[x->lists];
     int rc;
     keep_pool_memory();
@@ -159,15 +226,46 @@ int build_index(hc_index* x, cudaStream_t s) {
     if ((rc = status_of(upload_small(x->list_off_dev, x->list_off.data(),
                                      sizeof(uint64_t) * (x->lists + 1), s))))
         return rc;
+    if ((rc = dev_alloc_async((void**)&x->keys_hi, sizeof(uint64_t) * total, s))) return rc;
+    if (index_keeps_lo(x->params) &&
+        (rc = dev_alloc_async((void**)&x->keys_lo, sizeof(uint64_t) * total, s)))
+        return rc;
+    return dev_alloc_async((void**)&x->ids, sizeof(uint32_t) * total, s);
+}
+
+int index_new(const void* db, const hc_build_params* params, hc_index** out, hc_index** made) {
+    *made = nullptr;
+    if (!out) return HC_ERR_ARG;
+    *out = nullptr;
+    if (int rc = check_params(params)) return rc;
+    hc_index* x = new (std::nothrow) hc_index();
+    if (!x) return HC_ERR_OOM;
+    x->params = *params;
+    if (!x->params.partitions) x->params.partitions = 1;
+    if (params->dim_map)
+        x->dim_map.assign(params->dim_map, params->dim_map + params->curves * params->dims_per_curve);
+    x->params.dim_map = nullptr;
+    x->db = db;
+    *made = x;
+    return HC_OK;
+}
+
+}  // namespace hc
+
+namespace {
+
+// Algorithm 1 for an index whose params, db and dim_map are set.
+int build_index(hc_index* x, cudaStream_t s) {
+    const hc_build_params& P = x->params;
+    const uint32_t parts = P.partitions;
+    index_layout(x);
+    const uint64_t total = x->list_off[x->lists];
     // 16-coordinate keys: the high word holds 64 key bits and ties of it are
     // rare, so the index keeps high words only and recomputes a low word from
     // its row when a tie needs it (12 instead of 20 bytes per entry)
-    const bool keep_lo = P.dims_per_curve < 16;
-    if ((rc = dev_alloc_async((void**)&x->keys_hi, sizeof(uint64_t) * total, s))) return rc;
-    if (keep_lo && (rc = dev_alloc_async((void**)&x->keys_lo, sizeof(uint64_t) * total, s)))
-        return rc;
-    if ((rc = dev_alloc_async((void**)&x->ids, sizeof(uint32_t) * total, s))) return rc;
-
+    const bool keep_lo = index_keeps_lo(P);
+    int rc;
+    if ((rc = index_alloc(x, s))) return rc;
     // ids are implied by the slot: list L holds its partition's rows in id
     // order before the sort, so id = partition start + (slot - list start)
     std::vector<uint64_t> id_base(x->lists);
@@ -199,7 +297,10 @@ int build_index(hc_index* x, cudaStream_t s) {
 
     BuildKeysArgs ka{x->db, P.n, x->row_bytes, view_of(x).P, parts, x->list_off_dev, hi0, lo0,
                      nullptr};
-    rc = status_of(launch_build_keys(ka, s));
+    {
+        TraceRange tk("keys");
+        rc = status_of(launch_build_keys(ka, s));
+    }
     if (rc == HC_OK)
         rc = status_of(upload_small(id_base_dev, id_base.data(), sizeof(uint64_t) * x->lists, s));
     if (rc == HC_OK) {
@@ -208,27 +309,11 @@ int build_index(hc_index* x, cudaStream_t s) {
         sp.ids = nullptr;
         sp.id_base_dev = id_base_dev;
         sp.rows = RowKeys{x->db, x->row_bytes, view_of(x).P};
+        TraceRange ts("sort");
         rc = sort_segments(sp, sort_scratch, s);
     }
-    const int frc = status_of(cudaFreeAsync(scratch, s));
+    const int frc = status_of(pool_free(scratch, s));
     return rc ? rc : frc;
-}
-
-int new_index(const void* db, const hc_build_params* params, hc_index** out, hc_index** made) {
-    *made = nullptr;
-    if (!out) return HC_ERR_ARG;
-    *out = nullptr;
-    if (int rc = check_params(params)) return rc;
-    hc_index* x = new (std::nothrow) hc_index();
-    if (!x) return HC_ERR_OOM;
-    x->params = *params;
-    if (!x->params.partitions) x->params.partitions = 1;
-    if (params->dim_map)
-        x->dim_map.assign(params->dim_map, params->dim_map + params->curves * params->dims_per_curve);
-    x->params.dim_map = nullptr;
-    x->db = db;
-    *made = x;
-    return HC_OK;
 }
 
 }  // namespace
@@ -246,22 +331,25 @@ HC_API const char* hc_strerror(int status) {
         case HC_ERR_TIMEOUT: return "timed out";
         case HC_ERR_DEVICE_STATUS: return "a kernel reported an error status";
         case HC_ERR_STATE: return "object in the wrong state";
+        case HC_ERR_IO: return "file input/output failed";
+        case HC_ERR_FORMAT: return "not a valid index file for this database";
         default: return "unknown status";
     }
 }
 
 HC_API int hc_build(const void* db_dev, const hc_build_params* params, void* cuda_stream,
                     hc_index** out) {
+    TraceRange tr("hc_build");
     hc_index* x;
-    if (int rc = new_index(db_dev, params, out, &x)) return rc;
+    if (int rc = index_new(db_dev, params, out, &x)) return rc;
     if (!is_device_ptr(db_dev) || !aligned16(db_dev)) {
-        destroy(x);
+        index_destroy(x);
         return HC_ERR_ARG;
     }
     const int rc = build_index(x, static_cast<cudaStream_t>(cuda_stream));
     if (rc) {
         cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
-        destroy(x);
+        index_destroy(x);
         return rc;
     }
     *out = x;
@@ -270,9 +358,10 @@ HC_API int hc_build(const void* db_dev, const hc_build_params* params, void* cud
 
 HC_API int hc_build_host(const void* db_host, const hc_build_params* params, void* cuda_stream,
                          hc_index** out) {
+    TraceRange tr("hc_build_host");
     if (!db_host) return HC_ERR_ARG;
     hc_index* x;
-    if (int rc = new_index(nullptr, params, out, &x)) return rc;
+    if (int rc = index_new(nullptr, params, out, &x)) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const size_t bytes = (size_t)params->n * row_bytes_of(params->dtype, params->d);
     keep_pool_memory();
@@ -283,21 +372,22 @@ HC_API int hc_build_host(const void* db_host, const hc_build_params* params, voi
     const int src = status_of(cudaStreamSynchronize(s));
     if (!rc) rc = src;
     if (rc) {
-        destroy(x);
+        index_destroy(x);
         return rc;
     }
     *out = x;
     return HC_OK;
 }
 
-HC_API void hc_free(hc_index* idx) { destroy(idx); }
+HC_API void hc_free(hc_index* idx) { index_destroy(idx); }
 
 HC_API void hc_free_async(hc_index* idx, void* cuda_stream) {
-    destroy(idx, static_cast<cudaStream_t>(cuda_stream));
+    index_destroy(idx, static_cast<cudaStream_t>(cuda_stream));
 }
 
 HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
                     int32_t* out_ids_dev, void* out_dist_dev, void* cuda_stream) {
+    TraceRange tr("hc_query");
     if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
     if (nq == 0) return HC_OK;
     if (!q_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev)) return HC_ERR_ARG;
@@ -310,6 +400,7 @@ HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, u
 HC_API int hc_query_depths(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k,
                            const uint32_t* p_dev, int32_t* out_ids_dev, void* out_dist_dev,
                            void* cuda_stream) {
+    TraceRange tr("hc_query_depths");
     if (!idx || k < 1 || k > 128) return HC_ERR_ARG;
     if (nq == 0) return HC_OK;
     if (!q_dev || !p_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev)) return HC_ERR_ARG;
@@ -323,6 +414,7 @@ HC_API int hc_query_depths(hc_index* idx, const void* q_dev, uint32_t nq, uint32
 HC_API int hc_query_at(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
                        const int64_t* pos_dev, int32_t* out_ids_dev, void* out_dist_dev,
                        void* cuda_stream) {
+    TraceRange tr("hc_query_at");
     if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
     if (nq == 0) return HC_OK;
     if (!q_dev || !pos_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev))
@@ -376,6 +468,7 @@ HC_API size_t hc_query_ordered_workspace(uint32_t nq) { return nq ? order_layout
 HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
                             int32_t* out_ids_dev, void* out_dist_dev, void* workspace_dev,
                             size_t workspace_bytes, void* cuda_stream) {
+    TraceRange tr("hc_query_ordered");
     if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
     if (nq == 0) return HC_OK;
     if (!q_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev) || !workspace_dev ||
@@ -404,13 +497,18 @@ HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint3
     sp.out_hi = reinterpret_cast<uint64_t*>(ws + L.out_hi);
     sp.out_lo = reinterpret_cast<uint64_t*>(ws + L.out_lo);
     sp.out_ids = reinterpret_cast<uint32_t*>(ws + L.order);
-    if ((rc = sort_segments(sp, ws + L.sort, s))) return rc;
+    {
+        TraceRange to("order");
+        if ((rc = sort_segments(sp, ws + L.sort, s))) return rc;
+    }
+    TraceRange tq("walk");
     return status_of(launch_query(v, q_dev, nq, k, p, out_ids_dev, out_dist_dev, s, nullptr,
                                   nullptr, sp.out_ids));
 }
 
 HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids_host, void* out_dist_host, void* cuda_stream) {
+    TraceRange tr("hc_query_host");
     if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
     if (nq == 0) return HC_OK;
     if (!q_host || !out_ids_host || !out_dist_host) return HC_ERR_ARG;
@@ -485,6 +583,7 @@ HC_API int hc_index_copy_lists(const hc_index* idx, uint64_t* keys_hi_dev, uint6
 HC_API int hc_hilbert_keys(const void* x_dev, hc_dtype dtype, uint64_t count, uint32_t d,
                            uint32_t curves, uint32_t m, const uint32_t* dim_map_host,
                            uint64_t* hi_dev, uint64_t* lo_dev, void* cuda_stream) {
+    TraceRange tr("hc_hilbert_keys");
     if (dtype != HC_U8 && dtype != HC_F32) return HC_ERR_ARG;
     if (d < 1 || d > 4096 || curves < 1 || curves > 32 || m < 1 || m > 16) return HC_ERR_ARG;
     const uint32_t rb = row_bytes_of(dtype, d);
@@ -506,7 +605,7 @@ HC_API int hc_hilbert_keys(const void* x_dev, hc_dtype dtype, uint64_t count, ui
         if ((rc = dev_alloc_async((void**)&dm, sizeof(uint32_t) * curves * m, s))) return rc;
         if ((rc = status_of(cudaMemcpyAsync(dm, dim_map_host, sizeof(uint32_t) * curves * m,
                                             cudaMemcpyHostToDevice, s)))) {
-            cudaFreeAsync(dm, s);
+            pool_free(dm, s);
             return rc;
         }
     }
@@ -515,7 +614,7 @@ HC_API int hc_hilbert_keys(const void* x_dev, hc_dtype dtype, uint64_t count, ui
     if (dm) {
         // the copy above reads a host buffer the caller may free after return
         cudaStreamSynchronize(s);
-        cudaFreeAsync(dm, s);
+        pool_free(dm, s);
     }
     return rc;
 }
@@ -523,6 +622,7 @@ HC_API int hc_hilbert_keys(const void* x_dev, hc_dtype dtype, uint64_t count, ui
 HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
                         const uint64_t* seg_off_host, uint32_t nseg, uint32_t key_bits,
                         void* cuda_stream) {
+    TraceRange tr("hc_sort_keys");
     if (!seg_off_host || nseg < 1 || key_bits < 1 || key_bits > 128) return HC_ERR_ARG;
     for (uint32_t i = 0; i < nseg; ++i)
         if (seg_off_host[i + 1] < seg_off_host[i]) return HC_ERR_ARG;
@@ -561,13 +661,14 @@ HC_API int hc_sort_keys(uint64_t* hi_dev, uint64_t* lo_dev, uint32_t* ids_dev,
     if (!rc) rc = status_of(cudaMemcpyAsync(lo_dev, sp.out_lo, 8 * total, cudaMemcpyDeviceToDevice, s));
     if (!rc)
         rc = status_of(cudaMemcpyAsync(ids_dev, sp.out_ids, 4 * total, cudaMemcpyDeviceToDevice, s));
-    const int frc = status_of(cudaFreeAsync(buf, s));
+    const int frc = status_of(pool_free(buf, s));
     const int src = status_of(cudaStreamSynchronize(s));
     return rc ? rc : (frc ? frc : src);
 }
 
 HC_API int hc_query_positions(hc_index* idx, const void* q_dev, uint32_t nq, int64_t* pos_dev,
                               void* cuda_stream) {
+    TraceRange tr("hc_query_positions");
     if (!idx) return HC_ERR_ARG;
     if (nq == 0) return HC_OK;
     if (!is_device_ptr(q_dev) || !aligned16(q_dev) || !is_device_ptr(pos_dev)) return HC_ERR_ARG;
@@ -578,6 +679,7 @@ HC_API int hc_query_positions(hc_index* idx, const void* q_dev, uint32_t nq, int
 HC_API int hc_bruteforce(const void* db_dev, hc_dtype dtype, uint64_t n, uint32_t d,
                          const void* q_dev, uint32_t nq, uint32_t k, int32_t* out_ids_dev,
                          void* out_dist_dev, void* cuda_stream) {
+    TraceRange tr("hc_bruteforce");
     if (dtype != HC_U8 && dtype != HC_F32) return HC_ERR_ARG;
     if (k < 1 || k > 128 || d < 1 || d > 4096 || n >= (1ull << 31)) return HC_ERR_ARG;
     if (row_bytes_of(dtype, d) % 16) return HC_ERR_ARG;
@@ -587,6 +689,47 @@ HC_API int hc_bruteforce(const void* db_dev, hc_dtype dtype, uint64_t n, uint32_
         return HC_ERR_ARG;
     return status_of(launch_bruteforce(db_dev, dtype, n, d, q_dev, nq, k, out_ids_dev, out_dist_dev,
                                        static_cast<cudaStream_t>(cuda_stream)));
+}
+
+HC_API int hc_check_status(hc_check_report* out, int reset) {
+    if (!out) return HC_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+#ifdef HC_CHECK
+    out->enabled = 1;
+    if (cudaDeviceSynchronize() != cudaSuccess) return HC_ERR_CUDA;
+    {
+        // guards of the buffers still alive
+        std::lock_guard<std::mutex> g(g_guard_mu);
+        for (const auto& kv : g_guards) {
+            unsigned char h[kGuardBytes];
+            if (cudaMemcpy(h, static_cast<const char*>(kv.first) + kv.second, kGuardBytes,
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+                return HC_ERR_CUDA;
+            for (size_t i = 0; i < kGuardBytes; ++i) {
+                if (h[i] == kGuardByte) continue;
+                if (!out->violations) {
+                    out->site = kSitePad;
+                    out->index = i;
+                    out->bound = 0;
+                }
+                ++out->violations;
+            }
+        }
+    }
+    for (CheckReader r : check_readers()) {
+        CheckRecord rec{};
+        if (r(&rec, reset != 0) != 0) return HC_ERR_CUDA;
+        if (rec.count && !out->violations) {
+            out->site = rec.site;
+            out->index = rec.index;
+            out->bound = rec.bound;
+        }
+        out->violations += rec.count;
+    }
+#else
+    (void)reset;
+#endif
+    return HC_OK;
 }
 
 HC_API uint64_t hc_launch_count(void) { return g_launches.load(); }

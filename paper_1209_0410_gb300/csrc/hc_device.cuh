@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "hc.h"
+#include "hc_check.cuh"
 
 namespace hc {
 

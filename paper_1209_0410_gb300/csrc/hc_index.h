@@ -38,8 +38,29 @@ inline IndexView view_of(const hc_index* x) {
     v.keys_hi = x->keys_hi;
     v.keys_lo = x->keys_lo;
     v.ids = x->ids;
+    v.rows = x->params.n;
     return v;
 }
+
+// Index set-up shared by the entry points that make an index (api.cu:
+// hc_build, hc_build_host; persist.cu: hc_load).
+int status_of(cudaError_t e);
+bool aligned16(const void* p);
+// true when p is device memory of the current device (or managed)
+bool is_device_ptr(const void* p);
+// a new index object for these parameters (checked; HC_ERR_ARG when they are
+// invalid), nothing allocated on the device yet
+int index_new(const void* db, const hc_build_params* params, hc_index** out, hc_index** made);
+// lists, row_bytes and list_off from the parameters (Sec. 4.1: partition j
+// holds ids [floor(j n / l), floor((j + 1) n / l)))
+void index_layout(hc_index* x);
+// whether the lists store low key words (keys of fewer than 16 coordinates)
+bool index_keeps_lo(const hc_build_params& P);
+// the device arrays of a laid-out index: list offsets and dim map (both
+// uploaded), keys and ids (uninitialised), from the stream-ordered pool on s
+int index_alloc(hc_index* x, cudaStream_t s);
+// frees in stream order on s (default: the legacy stream)
+void index_destroy(hc_index* x, cudaStream_t s = cudaStreamLegacy);
 
 }  // namespace hc
 

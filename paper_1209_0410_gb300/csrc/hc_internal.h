@@ -97,6 +97,7 @@ struct IndexView {
     const uint64_t* keys_hi;
     const uint64_t* keys_lo;   // null: low words recomputed from the rows (16-coordinate keys)
     const uint32_t* ids;
+    uint64_t rows;             // database rows (bound of the row ids)
 };
 
 // p_query (device, nq entries, nullable) gives each query its own depth.

@@ -140,7 +140,9 @@ __device__ __forceinline__ void chunk_candidates_n(const uint8_t* __restrict__ d
 // Low key word of entry g (global entry index) of list L.
 __device__ __forceinline__ uint64_t entry_key_lo(const IndexView& ix, uint32_t L, uint64_t g) {
     if (ix.keys_lo) return __ldg(ix.keys_lo + g);
-    return row_key_lo(ix.db, ix.row_bytes, ix.P, __ldg(ix.ids + g), L % ix.P.curves);
+    const uint32_t id = __ldg(ix.ids + g);
+    return row_key_lo(ix.db, ix.row_bytes, ix.P, HC_IN_BOUNDS(kSiteRow, id, ix.rows) ? id : 0u,
+                      L % ix.P.curves);
 }
 
 // first i in [0, n) of list L (entries off ..) with key[i] >= (kh, kl), else n;
@@ -150,6 +152,7 @@ __device__ __forceinline__ uint32_t lower_bound_key(const IndexView& ix, uint32_
     uint32_t first = 0, count = n;
     while (count > 0) {
         const uint32_t step = count >> 1, mid = first + step;
+        if (!HC_IN_BOUNDS(kSiteSearch, mid, n)) break;
         const uint64_t h = __ldg(ix.keys_hi + off + mid);
         bool less = h < kh;
         if (h == kh) less = entry_key_lo(ix, L, off + mid) < kl;
@@ -211,10 +214,11 @@ __device__ __forceinline__ void search_lists(const IndexView& ix, const uint8_t*
         const uint32_t pos = pos_w[L];
         const uint32_t lo = pos > depth ? pos - depth : 0u;
         const uint32_t hi = (uint64_t)pos + depth < (uint64_t)n ? pos + depth : n;
+        if (!HC_IN_BOUNDS(kSiteWindow, hi, (uint64_t)n + 1)) continue;
         const uint32_t* idl = ix.ids + off;
         uint32_t next = lo + (uint32_t)lane < hi ? __ldg(idl + lo + lane) : 0u;
         for (uint32_t base = lo; base < hi; base += 32) {
-            const uint32_t id = next;
+            const uint32_t id = HC_IN_BOUNDS(kSiteRow, next, ix.rows) ? next : 0u;
             const uint32_t cnt = min(32u, hi - base);
             if (base + 32 < hi)
                 next = base + 32 + (uint32_t)lane < hi ? __ldg(idl + base + 32 + lane) : 0u;
@@ -266,7 +270,7 @@ __device__ __forceinline__ uint32_t pack_windows(const IndexView& ix, uint32_t d
             const uint32_t pos = pos_w[L];
             const uint32_t lo = pos > depth ? pos - depth : 0u;
             const uint32_t hi = (uint64_t)pos + depth < (uint64_t)n ? pos + depth : n;
-            len = hi > lo ? hi - lo : 0u;
+            len = hi > lo && HC_IN_BOUNDS(kSiteWindow, hi, (uint64_t)n + 1) ? hi - lo : 0u;
             at = (uint32_t)(off + lo);   // index entries < 2^32
         }
         uint32_t x = len;
@@ -303,7 +307,10 @@ __device__ __forceinline__ uint32_t packed_ids(const IndexView& ix, const uint32
             count = half;
         }
     }
-    return __ldg(ix.ids + win_at[lo] + (e - win_pre[lo]));
+    const uint64_t ent = (uint64_t)win_at[lo] + (e - win_pre[lo]);
+    if (!HC_IN_BOUNDS(kSiteEntry, ent, ix.list_off[ix.lists])) return 0u;
+    const uint32_t id = __ldg(ix.ids + ent);
+    return HC_IN_BOUNDS(kSiteRow, id, ix.rows) ? id : 0u;
 }
 
 // copies of one step: lane (c = lane % 8, g = lane / 8) moves vector c of

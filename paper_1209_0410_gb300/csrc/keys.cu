@@ -29,6 +29,8 @@ __global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const uint64_t g = a.list_off[part * a.P.curves + c + t] + local;
+                    if (!HC_IN_BOUNDS(kSiteKeySlot, g, a.list_off[a.partitions * a.P.curves]))
+                        continue;
                     a.hi[g] = hi[t];
                     if (a.lo) a.lo[g] = lo[t];
                     if (a.ids) a.ids[g] = (uint32_t)r;
@@ -39,6 +41,7 @@ __global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
             uint64_t hi, lo;
             curve_key(row, a.P, c, hi, lo);
             const uint64_t g = a.list_off[part * a.P.curves + c] + local;
+            if (!HC_IN_BOUNDS(kSiteKeySlot, g, a.list_off[a.partitions * a.P.curves])) continue;
             a.hi[g] = hi;
             if (a.lo) a.lo[g] = lo;
             if (a.ids) a.ids[g] = (uint32_t)r;

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "hc_index.h"
+#include "hc_trace.h"
 #include "hc_query_dev.cuh"
 
 using namespace hc;
@@ -379,6 +380,7 @@ __device__ void query_features(const IndexView& ix, const uint8_t* qrow, uint4 q
             const uint32_t lo = pos > 4 ? pos - 4 : 0u, hi = pos + 4 < n ? pos + 4 : n;
             valid = lo + j < hi;
             if (valid) id = __ldg(ix.ids + off + lo + j);
+            if (!HC_IN_BOUNDS(kSiteRow, id, ix.rows)) id = 0u;
         }
         uint64_t cands[ChunkWidth<8>::NG];
         chunk_candidates_n<false, 8>(db, ix.row_bytes, qrow, qv0, id, 32u, lane, cands);
@@ -669,6 +671,7 @@ extern "C" {
 
 HC_API int hc_features(hc_index* idx, const void* q_dev, uint32_t nq, float* feat_dev,
                        void* cuda_stream) {
+    TraceRange tr("hc_features");
     if (int rc = features_ok(idx)) return rc;
     if (nq == 0) return HC_OK;
     if (!dev_ptr(q_dev) || !dev_ptr(feat_dev) || ((uintptr_t)q_dev & 15)) return HC_ERR_ARG;
@@ -681,6 +684,7 @@ HC_API int hc_features(hc_index* idx, const void* q_dev, uint32_t nq, float* fea
 
 HC_API int hc_probe_labels(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k,
                            uint32_t p_max, uint32_t* p_min_dev, void* cuda_stream) {
+    TraceRange tr("hc_probe_labels");
     if (!idx || k < 1 || k > 128 || p_max > (1u << 30)) return HC_ERR_ARG;
     if (nq == 0) return HC_OK;
     if (!dev_ptr(q_dev) || !dev_ptr(p_min_dev) || ((uintptr_t)q_dev & 15)) return HC_ERR_ARG;
@@ -851,6 +855,7 @@ HC_API int hc_mlp_train_step(hc_mlp* M, const float* x_dev, const float* t_dev, 
 HC_API int hc_mlp_fit(hc_mlp* M, const float* feat_dev, const uint32_t* labels_dev, uint32_t n,
                       uint32_t epochs, uint32_t batch, float lr, uint64_t seed, float* losses_host,
                       void* cuda_stream) {
+    TraceRange tr("hc_mlp_fit");
     if (!M || batch < 1 || batch > M->max_batch || n < batch || epochs < 1 || !(lr > 0.f) ||
         !losses_host || !dev_ptr(feat_dev) || !dev_ptr(labels_dev))
         return HC_ERR_ARG;
@@ -968,6 +973,7 @@ HC_API int hc_mlp_forward(hc_mlp* M, const float* x_dev, uint32_t n, int bf16, f
 HC_API int hc_mlp_predict_depths(hc_mlp* M, hc_index* idx, const void* q_dev, uint32_t nq,
                                  float margin, uint32_t p_lo, uint32_t p_hi, uint32_t* p_dev,
                                  void* cuda_stream) {
+    TraceRange tr("hc_mlp_predict_depths");
     if (!M || features_ok(idx) != HC_OK || M->in != 4 * idx->params.curves) return HC_ERR_ARG;
     if (p_lo > p_hi || p_hi > (1u << 30)) return HC_ERR_ARG;
     if (nq == 0) return HC_OK;

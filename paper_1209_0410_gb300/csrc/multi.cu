@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "hc_index.h"
+#include "hc_trace.h"
 #include "hc_query_dev.cuh"
 
 using namespace hc;
@@ -66,6 +67,7 @@ __device__ void multi_query(const MultiJob& J, uint32_t qi, bool active, uint32_
                             uint32_t* pos_w, uint64_t* group_buf, uint8_t* ring, int lane) {
     WarpTopK<KR> top;
     top.init();
+    if (active && !HC_IN_BOUNDS(kSiteMultiQuery, qi, J.nq)) active = false;
     if (active) {
         const uint8_t* qrow = J.q + (size_t)qi * J.ix.row_bytes;
         if constexpr (LPR <= 8) {
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         if (t >= ntasks) return;
         const MultiTask T = tasks[t];
         const MultiJob& J = jobs[T.job];
+        if (!HC_IN_BOUNDS(kSiteMultiLists, J.ix.lists, kMaxLists + 1)) continue;
         const uint32_t group = warp / J.wpq, sub = warp % J.wpq;
         const uint32_t per_pass = nwarps / J.wpq;
         uint64_t* mb = merge + (size_t)(group * J.wpq) * 4 * 32;
@@ -319,6 +322,7 @@ HC_API int hc_multi_plan_create(const hc_multi_job* jobs, uint32_t njobs,
 }
 
 HC_API int hc_multi_run(hc_multi_plan* P, void* cuda_stream) {
+    TraceRange tr("hc_multi_run");
     if (!P) return HC_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if (P->exec) {
@@ -333,6 +337,7 @@ HC_API void hc_multi_plan_free(hc_multi_plan* P) { free_plan(P); }
 
 HC_API int hc_query_multi(const hc_multi_job* jobs, uint32_t njobs, const hc_multi_config* cfg,
                           void* cuda_stream) {
+    TraceRange tr("hc_query_multi");
     hc_multi_config c{8, 4, 2, 0};
     if (cfg) {
         c = *cfg;

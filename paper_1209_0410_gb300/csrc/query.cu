@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kerne
     const uint32_t w = blockIdx.x * kQWarps + warp;
     if (w >= a.nq) return;
     const uint32_t qi = a.order ? __ldg(a.order + w) : w;
+    if (!HC_IN_BOUNDS(kSiteQuery, qi, a.nq)) return;
     const IndexView& ix = a.ix;
     const uint8_t* qrow = static_cast<const uint8_t*>(a.q) + (size_t)qi * ix.row_bytes;
     const uint32_t depth = a.p_query ? __ldg(a.p_query + qi) : a.p;

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "hc_index.h"
+#include "hc_trace.h"
 
 using namespace hc;
 
@@ -227,6 +228,7 @@ Batch* form_batch(hc_server* S, int slot) {
 // Stages the batch (host copies into the pinned mirror) and enqueues copy-in,
 // the query kernel and copy-out on the slot's stream.  Called without the lock.
 int launch_batch(hc_server* S, Batch* b) {
+    TraceRange tr("serve_batch");
     const hc_index* ix = S->idx[b->index_id];
     const uint32_t rb = ix->row_bytes;
     char* hq = S->arena_host + b->q_off;

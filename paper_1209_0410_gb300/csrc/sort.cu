@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(kSThreads, 2) scatter_kernel(
     for (uint32_t i = t; i < count; i += kSThreads) {
         const uint64_t v = sm.w[padw(i)];
         const uint64_t g = sm.gbase[(uint32_t)(v >> shift) & 0xFFu] + i;
+        if (!HC_IN_BOUNDS(kSiteScatter, g - si.start, si.len)) continue;
         wdst[g] = v;
         pdst[g] = sm.p[padp(i)] + idoff;
         if (next_digit) next_digit[g] = (uint8_t)(v >> (shift + 8));
@@ -497,8 +498,11 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
         const uint32_t m = masks[warp][c];
         if ((m >> lane) & 1u) {
             const uint64_t r = slot + (uint32_t)__popc(m & lt_mask);
-            run_pos[r] = start + (warp * kFindChunks + (uint32_t)c) * 32 + (uint32_t)lane;
-            run_seg[r] = seg;
+            if (HC_IN_BOUNDS(kSiteRunList, r,
+                             (segs[nseg - 1].start + segs[nseg - 1].len) / 2)) {
+                run_pos[r] = start + (warp * kFindChunks + (uint32_t)c) * 32 + (uint32_t)lane;
+                run_seg[r] = seg;
+            }
         }
         slot += (uint32_t)__popc(m);
     }
@@ -508,7 +512,7 @@ __global__ void __launch_bounds__(256) sort_runs_kernel(
     uint64_t* hi, uint32_t* ids, int run_shift, RowKeys rows, const SegInfo* __restrict__ segs,
     const uint64_t* __restrict__ run_pos, const uint32_t* __restrict__ run_seg,
     const unsigned long long* __restrict__ nruns, uint4* __restrict__ long_list,
-    uint32_t* __restrict__ long_count) {
+    uint32_t* __restrict__ long_count, uint32_t long_cap) {
     static_assert(kMaxRun == 32, "one run record per lane");
     const int lane = threadIdx.x & 31;
     const uint64_t n = *nruns;
@@ -529,9 +533,11 @@ __global__ void __launch_bounds__(256) sort_runs_kernel(
         const uint32_t inmask = __ballot_sync(0xffffffffu, in);
         const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
         if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == rkey) {
-            if (lane == 0)
-                long_list[atomicAdd(long_count, 1u)] =
-                    make_uint4((uint32_t)rs, (uint32_t)(rs >> 32), seg, 0u);
+            if (lane == 0) {
+                const uint32_t li = atomicAdd(long_count, 1u);
+                if (HC_IN_BOUNDS(kSiteRunList, li, long_cap))
+                    long_list[li] = make_uint4((uint32_t)rs, (uint32_t)(rs >> 32), seg, 0u);
+            }
             continue;
         }
         const bool mine = (uint32_t)lane < len;
@@ -549,7 +555,7 @@ __global__ void __launch_bounds__(256) sort_runs_kernel(
             rank += (hu < h || (hu == h && (lu < l || (lu == l && du < d)))) ? 1u : 0u;
         }
         __syncwarp();
-        if (mine) {
+        if (mine && HC_IN_BOUNDS(kSiteRunWrite, rs + rank - segs[seg].start, segs[seg].len)) {
             hi[rs + rank] = h;
             ids[rs + rank] = d;
         }
@@ -620,7 +626,8 @@ __device__ void long_run_pass(const uint32_t* in, uint32_t* out, uint32_t n, int
             sm.hist[t] = run;
         }
         __syncthreads();
-        if (valid) out[sm.wcnt[warp][d] + __popc(peers & lt)] = r;
+        if (valid && HC_IN_BOUNDS(kSiteLongRun, sm.wcnt[warp][d] + __popc(peers & lt), n))
+            out[sm.wcnt[warp][d] + __popc(peers & lt)] = r;
         __syncthreads();
         for (int j = t; j < kRWarps * 256; j += kRThreads) (&sm.wcnt[0][0])[j] = 0;
         __syncthreads();
@@ -875,7 +882,7 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
                                                                 run_pos, run_seg, nruns);
             sort_runs_kernel<<<grid_stride_blocks(L.total / 64), 256, 0, s>>>(
                 p.out_hi, p.out_ids, 8 * skip, p.rows, segs, run_pos, run_seg, nruns, long_list,
-                long_count);
+                long_count, (uint32_t)(L.total / (kMaxRun + 1) + 1));
             // the word and position buffers are free now: scratch of the long runs
             long_run_kernel<<<std::min<uint32_t>(L.ntiles, 152), kRThreads, 0, s>>>(
                 p.out_hi, p.out_ids, wtmp, pa, pb, 8 * skip, p.rows, segs, long_list, long_count);

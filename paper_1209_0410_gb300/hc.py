@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libhc.so")
 HC_OK, HC_PENDING = 0, 1
 HC_ERR_ARG, HC_ERR_OOM, HC_ERR_CUDA, HC_ERR_BUDGET = -1, -2, -3, -4
 HC_ERR_TIMEOUT, HC_ERR_DEVICE_STATUS, HC_ERR_STATE = -5, -6, -7
+HC_ERR_IO, HC_ERR_FORMAT = -8, -9
 HC_U8, HC_F32 = 0, 1
 
 
@@ -69,77 +70,123 @@ _vp = ctypes.c_void_p
 _u32, _u64, _i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
 
 
+class _CheckReport(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_uint32), ("site", ctypes.c_uint32),
+                ("violations", ctypes.c_uint64), ("index", ctypes.c_uint64),
+                ("bound", ctypes.c_uint64)]
+
+
 def lib():
     """The loaded libhc.so; raises if it is not built."""
     global _LIB
     if _LIB is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libhc.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
-        L = ctypes.CDLL(LIB_PATH)
-        L.hc_strerror.restype = ctypes.c_char_p
-        L.hc_strerror.argtypes = [ctypes.c_int]
-        L.hc_build.argtypes = [_vp, ctypes.POINTER(_BuildParams), _vp, ctypes.POINTER(_vp)]
-        L.hc_build_host.argtypes = [_vp, ctypes.POINTER(_BuildParams), _vp, ctypes.POINTER(_vp)]
-        L.hc_query.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]
-        L.hc_query_host.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]
-        L.hc_free.argtypes = [_vp]
-        L.hc_free.restype = None
-        L.hc_free_async.argtypes = [_vp, _vp]
-        L.hc_free_async.restype = None
-        L.hc_index_describe.argtypes = [_vp, ctypes.POINTER(_IndexInfo), _vp]
-        L.hc_index_copy_lists.argtypes = [_vp, _vp, _vp, _vp, _vp]
-        L.hc_hilbert_keys.argtypes = [_vp, ctypes.c_int, _u64, _u32, _u32, _u32, _vp, _vp, _vp,
-                                      _vp]
-        L.hc_sort_keys.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _vp]
-        L.hc_sort_keys_noalloc.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _vp]
-        L.hc_query_positions.argtypes = [_vp, _vp, _u32, _vp, _vp]
-        L.hc_bruteforce.argtypes = [_vp, ctypes.c_int, _u64, _u32, _vp, _u32, _u32, _vp, _vp, _vp]
-        L.hc_query_depths.argtypes = [_vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]
-        L.hc_query_at.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp, _vp]
-        L.hc_query_ordered_workspace.restype = ctypes.c_size_t
-        L.hc_query_ordered_workspace.argtypes = [_u32]
-        L.hc_query_ordered.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp,
-                                       ctypes.c_size_t, _vp]
-        L.hc_serve_create_ex.argtypes = [ctypes.POINTER(_vp), _u32, _u64,
-                                         ctypes.POINTER(_ServeParams), ctypes.POINTER(_vp)]
-        L.hc_serve_create.argtypes = [ctypes.POINTER(_vp), _u32, _u64, ctypes.POINTER(_vp)]
-        L.hc_serve_submit.argtypes = [_vp, _u32, _vp, _u32, _u32, _u32,
-                                      ctypes.POINTER(ctypes.c_uint64)]
-        L.hc_serve_poll.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _u32]
-        L.hc_serve_stats_get.argtypes = [_vp, ctypes.POINTER(_ServeStats)]
-        L.hc_serve_poll_ex.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _u32,
-                                       ctypes.POINTER(ctypes.c_uint64)]
-        L.hc_serve_destroy.argtypes = [_vp]
-        L.hc_serve_destroy.restype = None
-        L.hc_features.argtypes = [_vp, _vp, _u32, _vp, _vp]
-        L.hc_probe_labels.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp]
-        L.hc_mlp_create.argtypes = [_u32, _u32, _u32, _u32, ctypes.POINTER(_vp)]
-        L.hc_mlp_param_count.argtypes = [_vp]
-        L.hc_mlp_param_count.restype = ctypes.c_uint32
-        L.hc_mlp_set_params.argtypes = [_vp, _vp, _vp, _vp]
-        L.hc_mlp_get_params.argtypes = [_vp, _vp, _vp, _vp]
-        L.hc_mlp_gradients.argtypes = [_vp, _vp, _vp, _u32, _vp, _vp, _vp]
-        L.hc_mlp_train_step.argtypes = [_vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp]
-        L.hc_mlp_forward.argtypes = [_vp, _vp, _u32, ctypes.c_int, _vp, _vp]
-        L.hc_mlp_predict_depths.argtypes = [_vp, _vp, _vp, _u32, ctypes.c_float, _u32, _u32, _vp,
-                                            _vp]
-        L.hc_mlp_free.argtypes = [_vp]
-        L.hc_mlp_free.restype = None
-        L.hc_serve_attach_predictor.argtypes = [_vp, _u32, _vp, ctypes.c_float, _u32, _u32]
-        L.hc_multi_plan_create.argtypes = [ctypes.POINTER(_MultiJob), _u32,
-                                           ctypes.POINTER(_MultiConfig), _vp, ctypes.POINTER(_vp)]
-        L.hc_multi_run.argtypes = [_vp, _vp]
-        L.hc_multi_plan_free.argtypes = [_vp]
-        L.hc_multi_plan_free.restype = None
-        L.hc_query_multi.argtypes = [ctypes.POINTER(_MultiJob), _u32, ctypes.POINTER(_MultiConfig),
-                                     _vp]
-        L.hc_launch_count.argtypes = []
-        L.hc_launch_count.restype = ctypes.c_uint64
-        L.hc_mlp_fit.argtypes = [_vp, _vp, _vp, _u32, _u32, _u32, ctypes.c_float, _u64, _vp, _vp]
-        L.hc_debug_fail_alloc.argtypes = [ctypes.c_long]
-        L.hc_debug_fail_alloc.restype = None
-        _LIB = L
+        _LIB = load_library(LIB_PATH)
     return _LIB
+
+
+def load_library(path):
+    """A libhc build (libhc.so or the bounds-checked libhc_check.so) loaded
+    from path with the argument types of every entry point."""
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built (%s); run __graft_entry__.build()"
+                           % (os.path.basename(path), path))
+    L = ctypes.CDLL(path)
+    L.hc_strerror.restype = ctypes.c_char_p
+    L.hc_strerror.argtypes = [ctypes.c_int]
+    L.hc_build.argtypes = [_vp, ctypes.POINTER(_BuildParams), _vp, ctypes.POINTER(_vp)]
+    L.hc_build_host.argtypes = [_vp, ctypes.POINTER(_BuildParams), _vp, ctypes.POINTER(_vp)]
+    L.hc_query.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]
+    L.hc_query_host.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]
+    L.hc_free.argtypes = [_vp]
+    L.hc_free.restype = None
+    L.hc_free_async.argtypes = [_vp, _vp]
+    L.hc_free_async.restype = None
+    L.hc_index_describe.argtypes = [_vp, ctypes.POINTER(_IndexInfo), _vp]
+    L.hc_index_copy_lists.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.hc_hilbert_keys.argtypes = [_vp, ctypes.c_int, _u64, _u32, _u32, _u32, _vp, _vp, _vp,
+                                  _vp]
+    L.hc_sort_keys.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _vp]
+    L.hc_sort_keys_noalloc.argtypes = [_vp, _vp, _vp, _vp, _u32, _u32, _vp]
+    L.hc_query_positions.argtypes = [_vp, _vp, _u32, _vp, _vp]
+    L.hc_bruteforce.argtypes = [_vp, ctypes.c_int, _u64, _u32, _vp, _u32, _u32, _vp, _vp, _vp]
+    L.hc_query_depths.argtypes = [_vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]
+    L.hc_query_at.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp, _vp]
+    L.hc_query_ordered_workspace.restype = ctypes.c_size_t
+    L.hc_query_ordered_workspace.argtypes = [_u32]
+    L.hc_query_ordered.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp,
+                                   ctypes.c_size_t, _vp]
+    L.hc_serve_create_ex.argtypes = [ctypes.POINTER(_vp), _u32, _u64,
+                                     ctypes.POINTER(_ServeParams), ctypes.POINTER(_vp)]
+    L.hc_serve_create.argtypes = [ctypes.POINTER(_vp), _u32, _u64, ctypes.POINTER(_vp)]
+    L.hc_serve_submit.argtypes = [_vp, _u32, _vp, _u32, _u32, _u32,
+                                  ctypes.POINTER(ctypes.c_uint64)]
+    L.hc_serve_poll.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _u32]
+    L.hc_serve_stats_get.argtypes = [_vp, ctypes.POINTER(_ServeStats)]
+    L.hc_serve_poll_ex.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _u32,
+                                   ctypes.POINTER(ctypes.c_uint64)]
+    L.hc_serve_destroy.argtypes = [_vp]
+    L.hc_serve_destroy.restype = None
+    L.hc_features.argtypes = [_vp, _vp, _u32, _vp, _vp]
+    L.hc_probe_labels.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp]
+    L.hc_mlp_create.argtypes = [_u32, _u32, _u32, _u32, ctypes.POINTER(_vp)]
+    L.hc_mlp_param_count.argtypes = [_vp]
+    L.hc_mlp_param_count.restype = ctypes.c_uint32
+    L.hc_mlp_set_params.argtypes = [_vp, _vp, _vp, _vp]
+    L.hc_mlp_get_params.argtypes = [_vp, _vp, _vp, _vp]
+    L.hc_mlp_gradients.argtypes = [_vp, _vp, _vp, _u32, _vp, _vp, _vp]
+    L.hc_mlp_train_step.argtypes = [_vp, _vp, _vp, _u32, ctypes.c_float, _vp, _vp]
+    L.hc_mlp_forward.argtypes = [_vp, _vp, _u32, ctypes.c_int, _vp, _vp]
+    L.hc_mlp_predict_depths.argtypes = [_vp, _vp, _vp, _u32, ctypes.c_float, _u32, _u32, _vp,
+                                        _vp]
+    L.hc_mlp_free.argtypes = [_vp]
+    L.hc_mlp_free.restype = None
+    L.hc_serve_attach_predictor.argtypes = [_vp, _u32, _vp, ctypes.c_float, _u32, _u32]
+    L.hc_multi_plan_create.argtypes = [ctypes.POINTER(_MultiJob), _u32,
+                                       ctypes.POINTER(_MultiConfig), _vp, ctypes.POINTER(_vp)]
+    L.hc_multi_run.argtypes = [_vp, _vp]
+    L.hc_multi_plan_free.argtypes = [_vp]
+    L.hc_multi_plan_free.restype = None
+    L.hc_query_multi.argtypes = [ctypes.POINTER(_MultiJob), _u32, ctypes.POINTER(_MultiConfig),
+                                 _vp]
+    L.hc_launch_count.argtypes = []
+    L.hc_launch_count.restype = ctypes.c_uint64
+    L.hc_mlp_fit.argtypes = [_vp, _vp, _vp, _u32, _u32, _u32, ctypes.c_float, _u64, _vp, _vp]
+    L.hc_save.argtypes = [_vp, ctypes.c_char_p, _vp]
+    L.hc_load.argtypes = [ctypes.c_char_p, _vp, _vp, ctypes.POINTER(_vp)]
+    L.hc_debug_fail_alloc.argtypes = [ctypes.c_long]
+    L.hc_debug_fail_alloc.restype = None
+    L.hc_check_status.argtypes = [ctypes.POINTER(_CheckReport), ctypes.c_int]
+    return L
+
+
+CHECK_LIB_PATH = os.path.join(_HERE, "libhc_check.so")
+
+
+class use_library:
+    """Routes this module's calls to another loaded build for a with-block,
+    e.g. ``with hc.use_library(hc.load_library(hc.CHECK_LIB_PATH)):``."""
+
+    def __init__(self, L):
+        self.L = L
+
+    def __enter__(self):
+        global _LIB
+        self.saved = _LIB
+        _LIB = self.L
+        return self.L
+
+    def __exit__(self, *exc):
+        global _LIB
+        _LIB = self.saved
+        return False
+
+
+def hc_check_status(reset=False):
+    """The checked build's report (enabled, site, violations, index, bound)."""
+    r = _CheckReport()
+    _check(lib().hc_check_status(ctypes.byref(r), 1 if reset else 0), "hc_check_status")
+    return dict(enabled=r.enabled, site=r.site, violations=r.violations, index=r.index,
+                bound=r.bound)
 
 
 def hc_strerror(status):
@@ -183,6 +230,7 @@ class Index:
 
     def __init__(self, handle, db, params):
         self.handle = handle
+        self._lib = lib()   # the build that made it frees it
         self.db = db
         self.dtype = params.dtype
         self.d = params.d
@@ -196,9 +244,9 @@ class Index:
         """Release the index; with a stream, in stream order on it (hc_free_async)."""
         if self.handle:
             if stream is None:
-                lib().hc_free(self.handle)
+                self._lib.hc_free(self.handle)
             else:
-                lib().hc_free_async(self.handle, _stream(stream))
+                self._lib.hc_free_async(self.handle, _stream(stream))
             self.handle = None
 
     def __del__(self):
@@ -365,6 +413,25 @@ def hc_index_copy_lists(index, stream=None):
                                          _dev(ids, "ids"), _stream(stream)),
                "hc_index_copy_lists")
     return hi, lo, ids, off
+
+
+def hc_save(index, path, stream=None):
+    """Writes the index's sorted lists to a file (the rows are not written)."""
+    _check(lib().hc_save(index.handle, os.fsencode(path), _stream(stream)), "hc_save")
+
+
+def hc_load(path, db, stream=None):
+    """An index from a file hc_save wrote, over the (n, d) CUDA tensor it indexes."""
+    h = ctypes.c_void_p()
+    _check(lib().hc_load(os.fsencode(path), _dev(db, "db"), _stream(stream), ctypes.byref(h)),
+           "hc_load")
+    info = _IndexInfo()
+    _check(lib().hc_index_describe(h, ctypes.byref(info), None), "hc_index_describe")
+    p = _BuildParams()
+    p.n, p.d, p.curves, p.dims_per_curve, p.bits = info.n, info.d, info.curves, \
+        info.dims_per_curve, 8
+    p.dtype, p.partitions = info.dtype, info.partitions
+    return Index(h, db, p)
 
 
 def hc_hilbert_keys(x, curves, dims_per_curve, dim_map=None, stream=None):

@@ -71,3 +71,21 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "from oracle" not in text and "import oracle" not in text, f
                 assert "hc_oracle" not in text and "liboracle" not in text, f
+
+
+def test_checked_build_exports_the_same_entry_points():
+    import subprocess
+    from paper_1209_0410_gb300 import _build
+    _build.build_hc_check()
+
+    def exported(path):
+        out = subprocess.run(["nm", "-D", "--defined-only", path], stdout=subprocess.PIPE,
+                             text=True).stdout
+        return {ln.split()[-1] for ln in out.splitlines() if " T hc_" in ln}
+
+    assert exported(_build.HC_CHECK_LIB) == exported(_build.HC_LIB)
+
+
+def test_normal_build_reports_checks_disabled(libhc):
+    from paper_1209_0410_gb300 import hc
+    assert hc.hc_check_status() == dict(enabled=0, site=0, violations=0, index=0, bound=0)
