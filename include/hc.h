@@ -123,6 +123,25 @@ HC_API int hc_build_host(const void* db_host, const hc_build_params* params, voi
                          hc_index** out);
 
 /*
+ * hc_build_host_async -- as hc_build_host, without waiting: the rows are
+ * copied from db_host into device memory the index owns on copy_stream, and
+ * the build is queued on cuda_stream behind that copy (an event), so that the
+ * upload of one database can run on the copy engine while the GPU still
+ * builds or queries another.
+ *   db_host      n x d rows in PAGE-LOCKED host memory (cudaHostAlloc or
+ *                cudaHostRegister; HC_ERR_ARG otherwise).  Read by the copy:
+ *                keep it alive and unchanged until cuda_stream has reached
+ *                the point of the call.
+ *   copy_stream  stream of the upload; NULL = cuda_stream (no overlap).
+ *   cuda_stream  the build, as for hc_build; the index is ready for later
+ *                work on cuda_stream (or on a stream that waits for it).
+ * The call returns once the work is queued.  Errors as hc_build; on an error
+ * the call waits for both streams and nothing of the index remains.
+ */
+HC_API int hc_build_host_async(const void* db_host, const hc_build_params* params,
+                               void* copy_stream, void* cuda_stream, hc_index** out);
+
+/*
  * hc_query -- Algorithm 2 for nq queries at once (queries grouped into one
  * GPU batch, Sec. 5.1), fused into one kernel: per query, the extended-key
  * of every curve's projection, lower_bound in each sorted list, the window
@@ -160,12 +179,31 @@ HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint3
 /*
  * hc_query_host -- hc_query from HOST buffers: copies the queries in, runs
  * the query kernel and copies the results back, on cuda_stream, and returns
- * once the results are in the host buffers.  Device staging buffers are
- * owned by the index and grow on demand (HC_ERR_OOM if they cannot).
- * Calls on the same index must not overlap (they share the staging).
+ * once the results are in the host buffers.  Batches of 4096 queries or more
+ * are answered in curve-0 key order as by hc_query_ordered (the same
+ * results).  Device staging buffers (queries, the ordering workspace,
+ * results) are owned by the index and grow on demand (HC_ERR_OOM if they
+ * cannot).  Calls on the same index must not overlap (they share the
+ * staging).
  */
 HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids_host, void* out_dist_host, void* cuda_stream);
+
+/*
+ * hc_query_host_async -- as hc_query_host, without waiting: the queries go up
+ * on copy_stream (NULL = cuda_stream), the walk and the copy of the results
+ * back run on cuda_stream behind them (an event), and the call returns once
+ * the work is queued.
+ *   q_host, out_ids_host, out_dist_host   PAGE-LOCKED host buffers
+ *                (HC_ERR_ARG otherwise), laid out as for hc_query_host; keep
+ *                them alive and q_host unchanged until cuda_stream reaches the
+ *                point of the call, which is also when the results are valid.
+ * A later host query on the same index waits, on its copy stream, until this
+ * call's results have left the staging.  Errors as hc_query_host.
+ */
+HC_API int hc_query_host_async(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k,
+                               uint32_t p, int32_t* out_ids_host, void* out_dist_host,
+                               void* copy_stream, void* cuda_stream);
 
 /*
  * hc_query_depths -- hc_query with one probe depth per query: p_dev holds nq

@@ -17,6 +17,17 @@ static std::atomic<uint64_t> g_launches{0};
 
 namespace hc {
 void count_launches(uint64_t n) { g_launches.fetch_add(n); }
+// true when p is page-locked host memory (cudaHostAlloc / cudaHostRegister)
+bool is_pinned_host(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
 }  // namespace hc
 
 namespace {
@@ -63,13 +74,6 @@ bool is_device_ptr(const void* p) {
 }  // namespace hc
 
 namespace {
-
-int dev_alloc(void** p, size_t bytes) {
-    *p = nullptr;
-    if (injected_failure()) return HC_ERR_OOM;
-    if (bytes == 0) bytes = 16;
-    return status_of(cudaMalloc(p, bytes));
-}
 
 #ifdef HC_CHECK
 // Checked build: every stream-ordered buffer is followed by a guard of
@@ -188,8 +192,9 @@ void index_destroy(hc_index* x, cudaStream_t s) {
     pool_free(x->keys_lo, s);
     pool_free(x->ids, s);
     pool_free(x->list_off_dev, s);
-    if (x->st_q) cudaFree(x->st_q);
-    if (x->st_out) cudaFree(x->st_out);
+    pool_free(x->st_q, s);
+    pool_free(x->st_out, s);
+    if (x->st_done) cudaEventDestroy(x->st_done);
     cudaGetLastError();
     delete x;
 }
@@ -379,6 +384,46 @@ HC_API int hc_build_host(const void* db_host, const hc_build_params* params, voi
     return HC_OK;
 }
 
+HC_API int hc_build_host_async(const void* db_host, const hc_build_params* params,
+                               void* copy_stream, void* cuda_stream, hc_index** out) {
+    TraceRange tr("hc_build_host_async");
+    hc_index* x;
+    if (int rc = index_new(nullptr, params, out, &x)) return rc;
+    if (!is_pinned_host(db_host)) {
+        index_destroy(x);
+        return HC_ERR_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaStream_t cs = copy_stream ? static_cast<cudaStream_t>(copy_stream) : s;
+    const size_t bytes = (size_t)params->n * row_bytes_of(params->dtype, params->d);
+    keep_pool_memory();
+    // the rows' buffer is allocated in the copy stream's order, so the upload
+    // waits for nothing queued on cuda_stream; the build waits for the upload
+    int rc = dev_alloc_async(&x->db_owned, bytes, cs);
+    x->db = x->db_owned;
+    cudaEvent_t landed = nullptr;
+    if (!rc) {
+        TraceRange tc("upload");
+        rc = status_of(cudaMemcpyAsync(x->db_owned, db_host, bytes, cudaMemcpyHostToDevice, cs));
+    }
+    if (!rc && cs != s) {
+        rc = status_of(cudaEventCreateWithFlags(&landed, cudaEventDisableTiming));
+        if (!rc) rc = status_of(cudaEventRecord(landed, cs));
+        if (!rc) rc = status_of(cudaStreamWaitEvent(s, landed, 0));
+    }
+    // destroying a recorded event is allowed: it is released once it completes
+    if (landed) cudaEventDestroy(landed);
+    if (!rc) rc = build_index(x, s);
+    if (rc) {
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(s);
+        index_destroy(x);
+        return rc;
+    }
+    *out = x;
+    return HC_OK;
+}
+
 HC_API void hc_free(hc_index* idx) { index_destroy(idx); }
 
 HC_API void hc_free_async(hc_index* idx, void* cuda_stream) {
@@ -438,6 +483,9 @@ struct OrderLayout {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// hc_query_host answers batches of at least this many queries in key order
+constexpr uint32_t kHostOrderedMin = 4096;
+
 SortProblem order_problem(uint32_t nq) {
     SortProblem sp;
     sp.seg_off = {0, (uint64_t)nq};
@@ -459,28 +507,12 @@ OrderLayout order_layout(uint32_t nq) {
     return L;
 }
 
-}  // namespace
 
-extern "C" {
-
-HC_API size_t hc_query_ordered_workspace(uint32_t nq) { return nq ? order_layout(nq).bytes : 0; }
-
-HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
-                            int32_t* out_ids_dev, void* out_dist_dev, void* workspace_dev,
-                            size_t workspace_bytes, void* cuda_stream) {
-    TraceRange tr("hc_query_ordered");
-    if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
-    if (nq == 0) return HC_OK;
-    if (!q_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev) || !workspace_dev ||
-        ((uintptr_t)workspace_dev & 255))
-        return HC_ERR_ARG;
+// hc_query_ordered's work on a checked workspace of order_layout(nq).bytes:
+// the curve-0 order keys, their sort, then the walk in that order.
+int enqueue_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
+                    int32_t* out_ids_dev, void* out_dist_dev, char* ws, cudaStream_t s) {
     const OrderLayout L = order_layout(nq);
-    if (workspace_bytes < L.bytes) return HC_ERR_ARG;
-    if (!is_device_ptr(q_dev) || !is_device_ptr(out_ids_dev) || !is_device_ptr(out_dist_dev) ||
-        !is_device_ptr(workspace_dev))
-        return HC_ERR_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    char* ws = static_cast<char*>(workspace_dev);
     uint64_t* keys = reinterpret_cast<uint64_t*>(ws + L.keys);
     uint64_t* seg = reinterpret_cast<uint64_t*>(ws + L.seg);
     const IndexView v = view_of(idx);
@@ -506,6 +538,90 @@ HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint3
                                   nullptr, sp.out_ids));
 }
 
+// hc_query_host's work: the queries up on cs (into the index's staging), the
+// walk on s behind them (in key order for large batches), the results down
+// on s.  The staging is reused by the next call on the index only after this
+// call's results have left (an event).
+int enqueue_host_query(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,
+                       int32_t* out_ids_host, void* out_dist_host, cudaStream_t cs,
+                       cudaStream_t s) {
+    const size_t qbytes = (size_t)nq * idx->row_bytes;
+    const size_t obytes = (size_t)nq * k * 4;
+    // large batches are answered in curve-0 key order (hc_query_ordered: the
+    // same results, fewer DRAM reads); its workspace follows the queries
+    const bool ordered = nq >= kHostOrderedMin;
+    const size_t ws_off = align256(qbytes);
+    const size_t st_bytes = ordered ? ws_off + order_layout(nq).bytes : qbytes;
+    int rc;
+    if (!idx->st_done &&
+        (rc = status_of(cudaEventCreateWithFlags(&idx->st_done, cudaEventDisableTiming))))
+        return rc;
+    // staging from the stream-ordered pool, replaced in stream order: no
+    // device-wide synchronisation, so work queued on other streams runs on;
+    // the query buffer is allocated in the copy stream's order
+    keep_pool_memory();
+    if ((rc = status_of(cudaStreamWaitEvent(cs, idx->st_done, 0)))) return rc;
+    if (st_bytes > idx->st_q_cap) {
+        pool_free(idx->st_q, cs);
+        idx->st_q = nullptr;
+        idx->st_q_cap = 0;
+        if ((rc = dev_alloc_async(&idx->st_q, st_bytes, cs))) return rc;
+        idx->st_q_cap = st_bytes;
+    }
+    if (2 * obytes > idx->st_out_cap) {
+        pool_free(idx->st_out, s);
+        idx->st_out = nullptr;
+        idx->st_out_cap = 0;
+        if ((rc = dev_alloc_async(&idx->st_out, 2 * obytes, s))) return rc;
+        idx->st_out_cap = 2 * obytes;
+    }
+    int32_t* d_ids = static_cast<int32_t*>(idx->st_out);
+    void* d_dist = static_cast<char*>(idx->st_out) + obytes;
+    if ((rc = status_of(cudaMemcpyAsync(idx->st_q, q_host, qbytes, cudaMemcpyHostToDevice, cs))))
+        return rc;
+    if (cs != s) {
+        cudaEvent_t landed = nullptr;
+        rc = status_of(cudaEventCreateWithFlags(&landed, cudaEventDisableTiming));
+        if (!rc) rc = status_of(cudaEventRecord(landed, cs));
+        if (!rc) rc = status_of(cudaStreamWaitEvent(s, landed, 0));
+        if (landed) cudaEventDestroy(landed);
+        if (rc) return rc;
+    }
+    rc = ordered ? enqueue_ordered(idx, idx->st_q, nq, k, p, d_ids, d_dist,
+                                   static_cast<char*>(idx->st_q) + ws_off, s)
+                 : status_of(launch_query(view_of(idx), idx->st_q, nq, k, p, d_ids, d_dist, s));
+    if (rc) return rc;
+    if ((rc = status_of(cudaMemcpyAsync(out_ids_host, d_ids, obytes, cudaMemcpyDeviceToHost, s))))
+        return rc;
+    if ((rc = status_of(cudaMemcpyAsync(out_dist_host, d_dist, obytes, cudaMemcpyDeviceToHost, s))))
+        return rc;
+    return status_of(cudaEventRecord(idx->st_done, s));
+}
+
+}  // namespace
+
+extern "C" {
+
+HC_API size_t hc_query_ordered_workspace(uint32_t nq) { return nq ? order_layout(nq).bytes : 0; }
+
+HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
+                            int32_t* out_ids_dev, void* out_dist_dev, void* workspace_dev,
+                            size_t workspace_bytes, void* cuda_stream) {
+    TraceRange tr("hc_query_ordered");
+    if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
+    if (nq == 0) return HC_OK;
+    if (!q_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev) || !workspace_dev ||
+        ((uintptr_t)workspace_dev & 255))
+        return HC_ERR_ARG;
+    const OrderLayout L = order_layout(nq);
+    if (workspace_bytes < L.bytes) return HC_ERR_ARG;
+    if (!is_device_ptr(q_dev) || !is_device_ptr(out_ids_dev) || !is_device_ptr(out_dist_dev) ||
+        !is_device_ptr(workspace_dev))
+        return HC_ERR_ARG;
+    return enqueue_ordered(idx, q_dev, nq, k, p, out_ids_dev, out_dist_dev,
+                           static_cast<char*>(workspace_dev), static_cast<cudaStream_t>(cuda_stream));
+}
+
 HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids_host, void* out_dist_host, void* cuda_stream) {
     TraceRange tr("hc_query_host");
@@ -513,34 +629,23 @@ HC_API int hc_query_host(hc_index* idx, const void* q_host, uint32_t nq, uint32_
     if (nq == 0) return HC_OK;
     if (!q_host || !out_ids_host || !out_dist_host) return HC_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const size_t qbytes = (size_t)nq * idx->row_bytes;
-    const size_t obytes = (size_t)nq * k * 4;
-    int rc;
-    if (qbytes > idx->st_q_cap) {
-        cudaStreamSynchronize(s);
-        cudaFree(idx->st_q);
-        idx->st_q_cap = 0;
-        if ((rc = dev_alloc(&idx->st_q, qbytes))) return rc;
-        idx->st_q_cap = qbytes;
-    }
-    if (2 * obytes > idx->st_out_cap) {
-        cudaStreamSynchronize(s);
-        cudaFree(idx->st_out);
-        idx->st_out_cap = 0;
-        if ((rc = dev_alloc(&idx->st_out, 2 * obytes))) return rc;
-        idx->st_out_cap = 2 * obytes;
-    }
-    int32_t* d_ids = static_cast<int32_t*>(idx->st_out);
-    void* d_dist = static_cast<char*>(idx->st_out) + obytes;
-    if ((rc = status_of(cudaMemcpyAsync(idx->st_q, q_host, qbytes, cudaMemcpyHostToDevice, s))))
-        return rc;
-    if ((rc = status_of(launch_query(view_of(idx), idx->st_q, nq, k, p, d_ids, d_dist, s))))
-        return rc;
-    if ((rc = status_of(cudaMemcpyAsync(out_ids_host, d_ids, obytes, cudaMemcpyDeviceToHost, s))))
-        return rc;
-    if ((rc = status_of(cudaMemcpyAsync(out_dist_host, d_dist, obytes, cudaMemcpyDeviceToHost, s))))
+    if (int rc = enqueue_host_query(idx, q_host, nq, k, p, out_ids_host, out_dist_host, s, s))
         return rc;
     return status_of(cudaStreamSynchronize(s));
+}
+
+HC_API int hc_query_host_async(hc_index* idx, const void* q_host, uint32_t nq, uint32_t k,
+                               uint32_t p, int32_t* out_ids_host, void* out_dist_host,
+                               void* copy_stream, void* cuda_stream) {
+    TraceRange tr("hc_query_host_async");
+    if (!idx || k < 1 || k > 128 || p > (1u << 30)) return HC_ERR_ARG;
+    if (nq == 0) return HC_OK;
+    if (!is_pinned_host(q_host) || !is_pinned_host(out_ids_host) ||
+        !is_pinned_host(out_dist_host))
+        return HC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaStream_t cs = copy_stream ? static_cast<cudaStream_t>(copy_stream) : s;
+    return enqueue_host_query(idx, q_host, nq, k, p, out_ids_host, out_dist_host, cs, s);
 }
 
 HC_API int hc_index_describe(const hc_index* idx, hc_index_info* info, uint64_t* list_off_host) {

@@ -22,6 +22,7 @@ struct hc_index {
     void* st_q = nullptr;
     void* st_out = nullptr;
     size_t st_q_cap = 0, st_out_cap = 0;
+    cudaEvent_t st_done = nullptr;   // the last host query's results have left
 };
 
 namespace hc {
@@ -48,6 +49,8 @@ int status_of(cudaError_t e);
 bool aligned16(const void* p);
 // true when p is device memory of the current device (or managed)
 bool is_device_ptr(const void* p);
+// true when p is page-locked host memory
+bool is_pinned_host(const void* p);
 // a new index object for these parameters (checked; HC_ERR_ARG when they are
 // invalid), nothing allocated on the device yet
 int index_new(const void* db, const hc_build_params* params, hc_index** out, hc_index** made);

@@ -95,8 +95,11 @@ def load_library(path):
     L.hc_strerror.argtypes = [ctypes.c_int]
     L.hc_build.argtypes = [_vp, ctypes.POINTER(_BuildParams), _vp, ctypes.POINTER(_vp)]
     L.hc_build_host.argtypes = [_vp, ctypes.POINTER(_BuildParams), _vp, ctypes.POINTER(_vp)]
+    L.hc_build_host_async.argtypes = [_vp, ctypes.POINTER(_BuildParams), _vp, _vp,
+                                      ctypes.POINTER(_vp)]
     L.hc_query.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]
     L.hc_query_host.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp]
+    L.hc_query_host_async.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp, _vp]
     L.hc_free.argtypes = [_vp]
     L.hc_free.restype = None
     L.hc_free_async.argtypes = [_vp, _vp]
@@ -293,6 +296,28 @@ def hc_build_host(db_host, curves=8, dims_per_curve=16, dim_map=None, partitions
     return Index(h, None, p)
 
 
+def hc_build_host_async(db_host, curves=8, dims_per_curve=16, dim_map=None, partitions=1,
+                        stream=None, copy_stream=None):
+    """hc_build_host without waiting: db_host is a pinned CPU tensor, uploaded on
+    copy_stream (None: the build stream) while the build waits behind it on
+    stream.  The index keeps db_host alive until it is freed."""
+    if not isinstance(db_host, torch.Tensor) or db_host.is_cuda or not db_host.is_pinned():
+        raise ValueError("db_host must be a pinned CPU tensor")
+    if not db_host.is_contiguous():
+        raise ValueError("db_host must be contiguous")
+    dtype = _dtype_code(db_host)
+    n, d = db_host.shape
+    p, keep = _params(n, d, dtype, curves, dims_per_curve, dim_map, partitions)
+    h = ctypes.c_void_p()
+    cs = _stream(copy_stream) if copy_stream is not None else None
+    _check(lib().hc_build_host_async(ctypes.c_void_p(db_host.data_ptr()), ctypes.byref(p), cs,
+                                     _stream(stream), ctypes.byref(h)), "hc_build_host_async")
+    del keep
+    idx = Index(h, None, p)
+    idx.host_rows = db_host
+    return idx
+
+
 def _dist_dtype(index_dtype):
     return torch.float32 if index_dtype == HC_F32 else torch.int32
 
@@ -382,6 +407,24 @@ def hc_query_host(index, q_host, k, p, out_ids=None, out_dist=None, stream=None)
                                    ctypes.c_void_p(out_ids.data_ptr()),
                                    ctypes.c_void_p(out_dist.data_ptr()), _stream(stream)),
                "hc_query_host")
+    return out_ids, out_dist
+
+
+def hc_query_host_async(index, q_host, k, p, out_ids, out_dist, stream=None,
+                        copy_stream=None):
+    """hc_query_host without waiting: pinned CPU tensors in and out; the results
+    are valid once `stream` reaches this point."""
+    for t, name in ((q_host, "q_host"), (out_ids, "out_ids"), (out_dist, "out_dist")):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_pinned() or \
+                not t.is_contiguous():
+            raise ValueError("%s must be a contiguous pinned CPU tensor" % name)
+    nq = q_host.shape[0]
+    if nq:
+        cs = _stream(copy_stream) if copy_stream is not None else None
+        _check(lib().hc_query_host_async(index.handle, ctypes.c_void_p(q_host.data_ptr()), nq,
+                                         k, p, ctypes.c_void_p(out_ids.data_ptr()),
+                                         ctypes.c_void_p(out_dist.data_ptr()), cs,
+                                         _stream(stream)), "hc_query_host_async")
     return out_ids, out_dist
 
 
