@@ -217,7 +217,7 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-BUILD_PASSES = 7   # radix passes of a 16-coordinate build: the top 7 bytes of the high word
+BUILD_PASSES = 6   # radix passes of a 16-coordinate build: the top 6 bytes of the high word
 
 
 def build_bytes(n, row_bytes, curves, passes=BUILD_PASSES):
@@ -232,7 +232,9 @@ def build_bytes(n, row_bytes, curves, passes=BUILD_PASSES):
     word per digit and 4096-record tile, four times), and the scatter (word
     and position in -- the first pass derives positions -- word and position
     out plus the next pass's digit byte; the last pass writes ids in place of
-    positions and no digit); then the run fix-up's read of the high words."""
+    positions and no digit); then the run fix-up's read of the high words and
+    ids (it reorders the short runs in place; the few records it moves are
+    not counted)."""
     r = curves * n
     algorithmic = n * row_bytes + r * 20 + passes * 2 * r * 20
     counts = 4 * 4 * 256 * (r / 4096.0)
@@ -242,7 +244,7 @@ def build_bytes(n, row_bytes, curves, passes=BUILD_PASSES):
         kernel += r * (8 if first else 1) + counts      # histogram + counts
         kernel += r * (8 if first else 12)              # scatter reads
         kernel += r * (12 if last else 13)              # scatter writes
-    kernel += r * 8                                     # run starts
+    kernel += r * 12                                    # run fix-up
     return float(algorithmic), float(kernel)
 
 

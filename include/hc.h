@@ -95,8 +95,8 @@ typedef struct {
  * hc_build -- Algorithm 1 on the GPU: for every partition and curve, the
  * extended-key of each row's projection, then a stable device radix sort of
  * (key, id), giving one list sorted by (key, id) per (partition, curve).  For
- * 16-coordinate curves the top 56 bits of the key are radix-sorted and runs
- * of equal 56-bit prefixes are then ordered by the whole key (the low word
+ * 16-coordinate curves the top 48 bits of the key are radix-sorted and runs
+ * of equal 48-bit prefixes are then ordered by the whole key (the low word
  * recomputed from the rows) and id; shorter keys are sorted by every byte.
  *   db_dev   n x d rows (uint8 or float32 per params->dtype), 16-byte aligned.
  *            NOT copied: the index keeps the pointer, so the caller keeps the

@@ -276,17 +276,18 @@ int build_index(hc_index* x, cudaStream_t s) {
     std::vector<uint64_t> id_base(x->lists);
     for (uint32_t L = 0; L < x->lists; ++L)
         id_base[L] = partition_start(L / P.curves, P.n, parts);
-    // 16-coordinate keys: the top 7 bytes of the high words are radix-sorted,
+    // 16-coordinate keys: the top 6 bytes of the high words are radix-sorted,
     // the last pass writing the final high words and ids, and runs of equal
-    // 56-bit prefixes are ordered by (high word, low word, id) on the device,
-    // the low words recomputed from the rows.  Shorter keys: every key byte
-    // is sorted (the low words are stored).  Neither waits on the host.
+    // 48-bit prefixes are ordered by (high word, low word, id) on the device,
+    // the low words recomputed from the rows where two high words tie.
+    // Shorter keys: every key byte is sorted (the low words are stored).
+    // Neither waits on the host.
     SortProblem sp;
     sp.seg_off = x->list_off;
     sp.seg_off_dev = x->list_off_dev;
     sp.key_bits = 8 * P.dims_per_curve;
     sp.allow_sync = false;
-    sp.hi_skip = keep_lo ? 0 : 1;
+    sp.hi_skip = keep_lo ? 0 : 2;
     sp.out_hi = x->keys_hi;
     sp.out_lo = x->keys_lo;
     sp.out_ids = x->ids;

@@ -49,12 +49,12 @@ struct RowKeys {
 };
 
 struct SortProblem {
-    const uint64_t* hi;        // device, total records
-    const uint64_t* lo;
-    const uint32_t* ids;
+    const uint64_t* hi = nullptr;   // device, total records
+    const uint64_t* lo = nullptr;
+    const uint32_t* ids = nullptr;
     std::vector<uint64_t> seg_off;  // host, nseg+1 (grid sizes)
-    const uint64_t* seg_off_dev;    // the same offsets on the device
-    uint32_t key_bits;         // 1..128
+    const uint64_t* seg_off_dev = nullptr;    // the same offsets on the device
+    uint32_t key_bits = 0;         // 1..128
     // With lo words (or gathered ids): may the sort synchronise the stream
     // once (to learn whether a run of equal high words is too long for the
     // high-word-first path)?  With false, every digit is sorted and nothing
@@ -71,9 +71,9 @@ struct SortProblem {
     // start on curve s % rows.P.curves, when a tie of the high words needs
     // it; out_lo is not written.
     RowKeys rows{};
-    uint64_t* out_hi;          // device, total records (distinct from sources)
-    uint64_t* out_lo;
-    uint32_t* out_ids;
+    uint64_t* out_hi = nullptr;   // device, total records (distinct from sources)
+    uint64_t* out_lo = nullptr;
+    uint32_t* out_ids = nullptr;
 };
 // Scratch bytes the sort needs for this problem (queried before allocating).
 size_t sort_scratch_bytes(const SortProblem& p);

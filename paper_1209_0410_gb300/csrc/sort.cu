@@ -14,10 +14,12 @@
 // low bytes left out) and a fix-up orders the short runs of equal prefixes by
 // (high word, low word, id).  For an index with affine ids and no stored low
 // words (hc_build) the last pass writes the final high words and ids and the
-// fix-up works in place and on the device alone: find_runs lists the run
-// starts, sort_runs orders each run of at most 32 records with one warp and
-// lists the longer ones, and long_run_kernel sorts those with one block each
-// through global memory.  Otherwise (low words stored, ids gathered) the
+// fix-up works in place and on the device alone: find_runs orders the short
+// runs inside 32-record chunks and lists the others, sort_runs orders each
+// listed run of at most 8 records with one lane and of at most 32 with one
+// warp, sort_mid_runs each run of up to 256 with one warp in shared memory,
+// and long_run_kernel the longer ones with one block each through global
+// memory.  Otherwise (low words stored, ids gathered) the
 // path is taken only when the caller may wait once on the stream: a run
 // longer than 32 then sends it back to sort by every byte.
 //
@@ -415,25 +417,37 @@ __global__ void __launch_bounds__(256) fixup_final_kernel(
 // In-place fix-up after a sort whose last pass wrote the final high words
 // and ids (affine ids, low words recomputed from rows).  Runs of equal
 // prefixes hi >> run_shift (ordered by id, i.e. by position) must end
-// ordered by (hi, low word, id).  Two kernels:
-//   find_runs  streams the high words (one tile per block, eight 32-record
-//              chunks of a warp loaded at once) and appends the position and
-//              segment of every run start to a list, one atomic per block;
-//   sort_runs  gives each listed run to one warp, one record per lane (at
-//              most kMaxRun = 32 records; a longer one is listed for
-//              long_run_kernel):
-//              lanes whose high words tie compute their low words, every lane
-//              counts the run's records below its own, and all lanes write
-//              after all have read.
-// A warp reading past its run's end sees only prefixes, which a permutation
-// inside another run leaves unchanged, so the in-place writes race with
-// nothing.
+// ordered by (hi, low word, id).  Four kernels, each reading what the one
+// before it listed:
+//   find_runs      streams the high words and ids and orders the short runs
+//                  inside each 32-record chunk (below), listing the others;
+//   sort_runs      listed runs: a lane per run of at most kLaneRun records
+//                  without equal high words, otherwise a warp per run of at
+//                  most kMaxRun = 32 (one record per lane: lanes whose high
+//                  words tie compute their low words, every lane counts the
+//                  run's records below its own, all write after all read),
+//                  listing longer ones;
+//   sort_mid_runs  a warp per run of at most kMidRun, ranked in shared memory;
+//   long_run       a block per longer run.
+// A reader past its run's end sees only prefixes, which a permutation inside
+// another run leaves unchanged, so the in-place writes race with nothing.
 constexpr int kFindWarps = 8;
 constexpr int kFindChunks = kTile / 32 / kFindWarps;   // 16 chunks of 32 records per warp
-constexpr int kFindBatch = 8;                          // chunks loaded at once
+constexpr int kFindBatch = 4;                          // chunks loaded at once
+constexpr int kLaneRun = 8;   // runs ordered inside find_runs: at most this long
 
+// find_runs: one tile per block, each warp four 32-record chunks at a time.
+// A run (records with equal prefixes hi >> run_shift) of at most kLaneRun
+// records that lies inside one chunk and has no two equal high words is
+// ordered right there: its records share the prefix, so each lane counts the
+// run's records whose low run_shift bits are below its own (32-bit shuffles)
+// and writes itself at run start + rank.  Every other run (longer, crossing a
+// chunk's edge, or with equal high words, which need the low words) has its
+// start listed for sort_runs.  A run's records are permuted among the run's
+// own positions, so the prefix at every position -- all that neighbouring
+// chunks read here -- never changes.  run_shift <= 32.
 __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
-    const uint64_t* __restrict__ hi, int run_shift, uint32_t nseg,
+    uint64_t* __restrict__ hi, uint32_t* __restrict__ ids, int run_shift, uint32_t nseg,
     const SegInfo* __restrict__ segs, uint64_t* __restrict__ run_pos,
     uint32_t* __restrict__ run_seg, unsigned long long* __restrict__ nruns) {
     static_assert(kFindChunks % kFindBatch == 0, "whole batches");
@@ -447,37 +461,85 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
     const uint64_t seg_end = si.start + si.len;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t low_mask = run_shift >= 32 ? 0xFFFFFFFFu : (1u << run_shift) - 1u;
     uint32_t found = 0;
     for (int c0 = 0; c0 < kFindChunks; c0 += kFindBatch) {
-        // a chunk's words, plus the word before it (lane 0) or after it (lane 31)
+        // a chunk's words and ids, plus the word before it (lane 0) or after
+        // it (lane 31)
         uint64_t hv[kFindBatch], halo[kFindBatch];
+        uint32_t dv[kFindBatch];
 #pragma unroll
         for (int j = 0; j < kFindBatch; ++j) {
             const uint32_t off = (warp * kFindChunks + (uint32_t)(c0 + j)) * 32 + (uint32_t)lane;
             const uint64_t i = start + off;
             const bool ok = off < count;
             hv[j] = ok ? __ldg(hi + i) : 0;
+            dv[j] = ok ? __ldg(ids + i) : 0u;
             uint64_t h = 0;
-            if (ok && lane == 0 && i > si.start) h = __ldg(hi + i - 1);
-            if (ok && lane == 31 && i + 1 < seg_end) h = __ldg(hi + i + 1);
+            if (ok && lane == 0 && i > si.start) h = hi[i - 1];
+            if (ok && lane == 31 && i + 1 < seg_end) h = hi[i + 1];
             halo[j] = h;
         }
 #pragma unroll
         for (int j = 0; j < kFindBatch; ++j) {
-            const uint32_t off = (warp * kFindChunks + (uint32_t)(c0 + j)) * 32 + (uint32_t)lane;
+            const uint32_t base = (warp * kFindChunks + (uint32_t)(c0 + j)) * 32;
+            const uint32_t off = base + (uint32_t)lane;
             const uint64_t i = start + off;
             const bool ok = off < count;
-            const uint64_t key = hv[j] >> run_shift;
+            const uint64_t w = hv[j];
+            const uint64_t key = w >> run_shift;
             // every lane takes part in both shuffles; the end lanes then use their halo
-            const uint64_t up = __shfl_up_sync(0xffffffffu, hv[j], 1);
-            const uint64_t dn = __shfl_down_sync(0xffffffffu, hv[j], 1);
+            const uint64_t up = __shfl_up_sync(0xffffffffu, w, 1);
+            const uint64_t dn = __shfl_down_sync(0xffffffffu, w, 1);
             const uint64_t prev = lane == 0 ? halo[j] : up;
             const uint64_t next = lane == 31 ? halo[j] : dn;
-            const bool run_start = ok && i + 1 < seg_end && (next >> run_shift) == key &&
-                                   !(i > si.start && (prev >> run_shift) == key);
-            const uint32_t starts = __ballot_sync(0xffffffffu, run_start);
-            if (lane == 0) masks[warp][c0 + j] = starts;
-            found += (uint32_t)__popc(starts);
+            const bool ps = ok && i > si.start && (prev >> run_shift) == key;   // run goes on before
+            const bool ns = ok && i + 1 < seg_end && (next >> run_shift) == key;  // ... and after
+            uint32_t listed = 0;
+            if (__ballot_sync(0xffffffffu, ps || ns)) {
+                // this lane's run inside the chunk: lanes s..e (cut at the chunk's edges)
+                const uint32_t brk = __ballot_sync(0xffffffffu, !ps);
+                const uint32_t ends = __ballot_sync(0xffffffffu, !ns);
+                const uint32_t below = brk & (0xFFFFFFFFu >> (31 - lane));
+                const uint32_t above = ends >> lane;
+                const bool cut = below == 0 || above == 0;   // the run crosses an edge
+                const int s = below ? 31 - __clz(below) : 0;
+                const int e = above ? lane + __ffs(above) - 1 : 31;
+                const bool in_run = ps || ns;
+                const uint32_t lw = (uint32_t)w & low_mask;
+                uint32_t rank = 0;
+                bool tie = false;
+                // offsets up to the chunk's longest run that can be ordered here
+                const int len0 = e - s + 1;
+                const int reach = __reduce_max_sync(
+                    0xffffffffu, (in_run && !cut && len0 <= kLaneRun) ? (uint32_t)len0 : 1u);
+                for (int o = 1; o < reach; ++o) {
+                    const uint32_t lu = __shfl_up_sync(0xffffffffu, lw, o);
+                    const uint32_t ld = __shfl_down_sync(0xffffffffu, lw, o);
+                    if (lane - o >= s) {
+                        rank += lu < lw ? 1u : 0u;
+                        tie |= lu == lw;
+                    }
+                    if (lane + o <= e) {
+                        rank += ld < lw ? 1u : 0u;
+                        tie |= ld == lw;
+                    }
+                }
+                const int len = e - s + 1;
+                const bool short_run = in_run && !cut && len <= kLaneRun;
+                const uint32_t ties = __ballot_sync(0xffffffffu, short_run && tie);
+                const bool run_tie = short_run && ((ties >> s) & ((1u << len) - 1u)) != 0;
+                const bool here = short_run && !run_tie;
+                // the run's true start lane lists a run not ordered here
+                listed = __ballot_sync(0xffffffffu, in_run && !ps && !here);
+                if (here && rank != (uint32_t)(lane - s)) {
+                    const uint64_t dst = start + base + (uint32_t)s + rank;
+                    hi[dst] = w;
+                    ids[dst] = dv[j];
+                }
+            }
+            if (lane == 0) masks[warp][c0 + j] = listed;
+            found += (uint32_t)__popc(listed);
         }
     }
     if (lane == 0) wbase[warp] = found;
@@ -508,6 +570,60 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
     }
 }
 
+// One listed run by the whole warp, one record per lane: a run longer than
+// kMaxRun goes to the long list; otherwise lanes whose high words tie compute
+// their low words, every lane counts the run's records below its own, and
+// all lanes write after all have read.
+__device__ __forceinline__ void warp_sort_run(uint64_t* hi, uint32_t* ids, int run_shift,
+                                              const RowKeys& rows, const SegInfo* segs,
+                                              uint64_t rs, uint32_t seg, uint4* long_list,
+                                              uint32_t* long_count, uint32_t long_cap,
+                                              int lane) {
+    const uint64_t seg_end = segs[seg].start + segs[seg].len;
+    const uint32_t curve = seg % rows.P.curves;
+    const uint64_t e = rs + lane;
+    const bool inseg = e < seg_end;
+    const uint64_t he = inseg ? hi[e] : ~0ull;
+    const uint32_t de = inseg ? ids[e] : 0xFFFFFFFFu;
+    const uint64_t rkey = __shfl_sync(0xffffffffu, he, 0) >> run_shift;
+    const bool in = inseg && (he >> run_shift) == rkey;
+    const uint32_t inmask = __ballot_sync(0xffffffffu, in);
+    const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
+    if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == rkey) {
+        if (lane == 0) {
+            const uint32_t li = atomicAdd(long_count, 1u);
+            if (HC_IN_BOUNDS(kSiteRunList, li, long_cap))
+                long_list[li] = make_uint4((uint32_t)rs, (uint32_t)(rs >> 32), seg, 0u);
+        }
+        return;
+    }
+    const bool mine = (uint32_t)lane < len;
+    const uint64_t h = mine ? he : ~0ull;
+    const uint32_t d = mine ? de : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, h);
+    const uint64_t l = (mine && __popc(peers) > 1)
+                           ? row_key_lo(rows.db, rows.row_bytes, rows.P, d, curve)
+                           : 0;
+    uint32_t rank = 0;
+    for (uint32_t u = 0; u < len; ++u) {
+        const uint64_t hu = __shfl_sync(0xffffffffu, h, (int)u);
+        const uint64_t lu = __shfl_sync(0xffffffffu, l, (int)u);
+        const uint32_t du = __shfl_sync(0xffffffffu, d, (int)u);
+        rank += (hu < h || (hu == h && (lu < l || (lu == l && du < d)))) ? 1u : 0u;
+    }
+    __syncwarp();
+    if (mine && HC_IN_BOUNDS(kSiteRunWrite, rs + rank - segs[seg].start, segs[seg].len)) {
+        hi[rs + rank] = h;
+        ids[rs + rank] = d;
+    }
+    __syncwarp();
+}
+
+// The runs find_runs listed, 32 per warp at a time.  First each lane takes
+// one: a run of at most kLaneRun records without two equal high words is
+// ordered by that lane alone (its records share the prefix, so the low
+// run_shift bits order them); then the warp takes the runs its lanes left,
+// one after another (warp_sort_run).
 __global__ void __launch_bounds__(256) sort_runs_kernel(
     uint64_t* hi, uint32_t* ids, int run_shift, RowKeys rows, const SegInfo* __restrict__ segs,
     const uint64_t* __restrict__ run_pos, const uint32_t* __restrict__ run_seg,
@@ -516,55 +632,179 @@ __global__ void __launch_bounds__(256) sort_runs_kernel(
     static_assert(kMaxRun == 32, "one run record per lane");
     const int lane = threadIdx.x & 31;
     const uint64_t n = *nruns;
+    const uint32_t low_mask = run_shift >= 32 ? 0xFFFFFFFFu : (1u << run_shift) - 1u;
     const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t r = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n;
-         r += nw) {
-        const uint64_t rs = __ldg(run_pos + r);
-        const uint32_t seg = __ldg(run_seg + r);
+    for (uint64_t r0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+         r0 < n; r0 += nw * 32) {
+        const uint64_t r = r0 + (uint64_t)lane;
+        uint64_t rs = 0;
+        uint32_t seg = 0;
+        bool left = false;
+        if (r < n) {
+            rs = __ldg(run_pos + r);
+            seg = __ldg(run_seg + r);
+            const uint64_t seg_end = segs[seg].start + segs[seg].len;
+            // the next kLaneRun + 1 words, all loads in flight at once
+            uint64_t hw[kLaneRun + 1];
+#pragma unroll
+            for (int t = 0; t <= kLaneRun; ++t) hw[t] = rs + t < seg_end ? hi[rs + t] : 0;
+            const uint64_t pre = hw[0] >> run_shift;
+            uint32_t lw[kLaneRun];
+            int len = 0;
+            bool more = true;
+#pragma unroll
+            for (int t = 0; t < kLaneRun; ++t) {
+                const bool in = more && rs + t < seg_end && (hw[t] >> run_shift) == pre;
+                lw[t] = in ? (uint32_t)hw[t] & low_mask : 0u;
+                if (in) len = t + 1;
+                more = in;
+            }
+            // longer than kLaneRun, or two equal high words: the warp's turn
+            left = more && rs + kLaneRun < seg_end && (hw[kLaneRun] >> run_shift) == pre;
+#pragma unroll
+            for (int a = 0; a < kLaneRun; ++a)
+#pragma unroll
+                for (int b = a + 1; b < kLaneRun; ++b)
+                    if (b < len && lw[a] == lw[b]) left = true;
+            if (!left) {
+                uint32_t dv[kLaneRun];
+#pragma unroll
+                for (int t = 0; t < kLaneRun; ++t) dv[t] = t < len ? ids[rs + t] : 0u;
+#pragma unroll
+                for (int t = 0; t < kLaneRun; ++t) {
+                    if (t < len) {
+                        uint32_t rank = 0;
+#pragma unroll
+                        for (int u = 0; u < kLaneRun; ++u)
+                            rank += (u < len && lw[u] < lw[t]) ? 1u : 0u;
+                        if (rank != (uint32_t)t &&
+                            HC_IN_BOUNDS(kSiteRunWrite, rs + rank - segs[seg].start,
+                                         segs[seg].len)) {
+                            hi[rs + rank] = hw[t];
+                            ids[rs + rank] = dv[t];
+                        }
+                    }
+                }
+            }
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, left);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint64_t rs2 = __shfl_sync(0xffffffffu, rs, src);
+            const uint32_t seg2 = __shfl_sync(0xffffffffu, seg, src);
+            warp_sort_run(hi, ids, run_shift, rows, segs, rs2, seg2, long_list, long_count,
+                          long_cap, lane);
+        }
+    }
+}
+
+// Runs of kMaxRun + 1 .. kMidRun records, as listed by sort_runs: one warp
+// per run (grid-stride over the list).  The warp finds the run's end, stages
+// its records in shared memory and ranks each record among them by (high
+// word, id); when two high words tie it computes every record's low word from
+// its row and ranks by (high word, low word, id).  A longer run is listed for
+// long_run_kernel.
+constexpr uint32_t kMidRun = 256;
+constexpr int kMidWarps = 8;
+
+struct MidRunSmem {
+    uint64_t h[kMidWarps][kMidRun];
+    uint64_t l[kMidWarps][kMidRun];
+    uint32_t d[kMidWarps][kMidRun];
+};
+
+__global__ void __launch_bounds__(kMidWarps * 32) sort_mid_runs_kernel(
+    uint64_t* hi, uint32_t* ids, int run_shift, RowKeys rows, const SegInfo* __restrict__ segs,
+    const uint4* __restrict__ long_list, const uint32_t* __restrict__ long_count,
+    uint4* __restrict__ vlong_list, uint32_t* __restrict__ vlong_count, uint32_t vlong_cap) {
+    __shared__ MidRunSmem sm;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = threadIdx.x >> 5;
+    uint64_t* sh = sm.h[warp];
+    uint64_t* sl = sm.l[warp];
+    uint32_t* sd = sm.d[warp];
+    const uint32_t total = *long_count;
+    const uint32_t nw = gridDim.x * kMidWarps;
+    for (uint32_t e = blockIdx.x * kMidWarps + warp; e < total; e += nw) {
+        const uint4 fe = long_list[e];
+        const uint64_t rs = ((uint64_t)fe.y << 32) | fe.x;
+        const uint32_t seg = fe.z;
         const uint64_t seg_end = segs[seg].start + segs[seg].len;
-        const uint32_t curve = seg % rows.P.curves;
-        // the run's records, one per lane, words and ids loaded together
-        const uint64_t e = rs + lane;
-        const bool inseg = e < seg_end;
-        const uint64_t he = inseg ? hi[e] : ~0ull;
-        const uint32_t de = inseg ? ids[e] : 0xFFFFFFFFu;
-        const uint64_t rkey = __shfl_sync(0xffffffffu, he, 0) >> run_shift;
-        const bool in = inseg && (he >> run_shift) == rkey;
-        const uint32_t inmask = __ballot_sync(0xffffffffu, in);
-        const uint32_t len = __ffs(~inmask) ? (uint32_t)(__ffs(~inmask) - 1) : 32u;
-        if (len == 32 && rs + 32 < seg_end && (hi[rs + 32] >> run_shift) == rkey) {
+        const uint64_t pre = hi[rs] >> run_shift;
+        // the run's length, looked at 32 records at a time up to kMidRun + 1
+        uint32_t n = 0;
+        for (uint32_t b = 0;; b += 32) {
+            const uint64_t i = rs + b + (uint32_t)lane;
+            const bool in = i < seg_end && (hi[i] >> run_shift) == pre;
+            const uint32_t m = __ballot_sync(0xffffffffu, in);
+            if (m != 0xffffffffu) {
+                n = b + (uint32_t)(__ffs(~m) - 1);
+                break;
+            }
+            if (b + 32 > kMidRun) {
+                n = kMidRun + 1;
+                break;
+            }
+        }
+        if (n > kMidRun) {
             if (lane == 0) {
-                const uint32_t li = atomicAdd(long_count, 1u);
-                if (HC_IN_BOUNDS(kSiteRunList, li, long_cap))
-                    long_list[li] = make_uint4((uint32_t)rs, (uint32_t)(rs >> 32), seg, 0u);
+                const uint32_t vi = atomicAdd(vlong_count, 1u);
+                if (HC_IN_BOUNDS(kSiteRunList, vi, vlong_cap)) vlong_list[vi] = fe;
             }
             continue;
         }
-        const bool mine = (uint32_t)lane < len;
-        const uint64_t h = mine ? he : ~0ull;
-        const uint32_t d = mine ? de : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, h);
-        const uint64_t l = (mine && __popc(peers) > 1)
-                               ? row_key_lo(rows.db, rows.row_bytes, rows.P, d, curve)
-                               : 0;
-        uint32_t rank = 0;
-        for (uint32_t u = 0; u < len; ++u) {
-            const uint64_t hu = __shfl_sync(0xffffffffu, h, (int)u);
-            const uint64_t lu = __shfl_sync(0xffffffffu, l, (int)u);
-            const uint32_t du = __shfl_sync(0xffffffffu, d, (int)u);
-            rank += (hu < h || (hu == h && (lu < l || (lu == l && du < d)))) ? 1u : 0u;
+        bool tie = false;
+        for (uint32_t i = lane; i < n; i += 32) {
+            sh[i] = hi[rs + i];
+            sd[i] = ids[rs + i];
         }
         __syncwarp();
-        if (mine && HC_IN_BOUNDS(kSiteRunWrite, rs + rank - segs[seg].start, segs[seg].len)) {
-            hi[rs + rank] = h;
-            ids[rs + rank] = d;
+        for (uint32_t i = lane; i < n; i += 32)
+            for (uint32_t j = 0; j < n; ++j) tie |= j != i && sh[j] == sh[i];
+        const bool need_lo = __any_sync(0xffffffffu, tie);
+        if (need_lo) {
+            const uint32_t curve = seg % rows.P.curves;
+            for (uint32_t i = lane; i < n; i += 32)
+                sl[i] = row_key_lo(rows.db, rows.row_bytes, rows.P, sd[i], curve);
+            __syncwarp();
+        }
+        uint32_t rk[kMidRun / 32];
+#pragma unroll
+        for (int t = 0; t < (int)(kMidRun / 32); ++t) {
+            const uint32_t i = (uint32_t)lane + 32u * (uint32_t)t;
+            uint32_t r = 0;
+            if (i < n) {
+                const uint64_t hx = sh[i];
+                const uint32_t dx = sd[i];
+                const uint64_t lx = need_lo ? sl[i] : 0;
+                for (uint32_t j = 0; j < n; ++j) {
+                    const uint64_t hj = sh[j];
+                    bool before = hj < hx;
+                    if (hj == hx) {
+                        const uint64_t lj = need_lo ? sl[j] : 0;
+                        before = lj < lx || (lj == lx && sd[j] < dx);
+                    }
+                    r += before ? 1u : 0u;
+                }
+            }
+            rk[t] = r;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < (int)(kMidRun / 32); ++t) {
+            const uint32_t i = (uint32_t)lane + 32u * (uint32_t)t;
+            if (i < n && HC_IN_BOUNDS(kSiteRunWrite, rk[t], n)) {
+                hi[rs + rk[t]] = sh[i];
+                ids[rs + rk[t]] = sd[i];
+            }
         }
         __syncwarp();
     }
 }
 
-// Runs of more than kMaxRun records with equal prefixes hi >> run_shift, as
-// listed by sort_runs: one block per run (grid-stride over the list; with an
+// Runs of more than kMidRun records with equal prefixes hi >> run_shift, as
+// listed by sort_mid_runs: one block per run (grid-stride over the list; with an
 // empty list every block returns at once).  A run's records arrive in id
 // order; stable 8-bit passes over the bytes in which their low words (from
 // the rows), then the bits of their high words below run_shift, differ leave
@@ -732,7 +972,7 @@ struct Layout {
     uint32_t nseg = 0, ntiles = 0;
     uint64_t ncounts = 0;
     size_t off_w = 0, off_pa = 0, off_pb = 0, off_counts = 0, off_totals = 0, off_segs = 0,
-           off_flag = 0, off_digits = 0, off_long = 0, bytes = 0;
+           off_flag = 0, off_digits = 0, off_long = 0, off_vlong = 0, bytes = 0;
 };
 
 Layout make_layout(const SortProblem& p) {
@@ -752,12 +992,27 @@ Layout make_layout(const SortProblem& p) {
     L.off_counts = o;  o = align_up(o + sizeof(uint32_t) * (L.ncounts ? L.ncounts : 1));
     L.off_totals = o;  o = align_up(o + sizeof(uint32_t) * 256 * (L.nseg ? L.nseg : 1));
     L.off_segs = o;    o = align_up(o + sizeof(SegInfo) * (L.nseg ? L.nseg : 1));
-    L.off_flag = o;    o = align_up(o + 16);   // flag word; run count at +8
+    L.off_flag = o;    o = align_up(o + 32);   // flag, long count (+4), run count (+8), very long count (+16)
     L.off_digits = o;  o = align_up(o + L.total);
     // runs longer than kMaxRun: at most total / (kMaxRun + 1) of them
     L.off_long = o;    o = align_up(o + sizeof(uint4) * (L.total / (kMaxRun + 1) + 1));
+    // runs longer than kMidRun in the in-place fix-up (a sort without low
+    // words), at most total / (kMidRun + 1).  Callers size the scratch before
+    // they set the ids, so the region depends on the low words alone: a
+    // problem sized without them never needs more than was reserved.
+    L.off_vlong = o;
+    if (p.lo == nullptr) o = align_up(o + sizeof(uint4) * (L.total / (kMidRun + 1) + 1));
     L.bytes = o;
     return L;
+}
+
+// min(cap, per_sm x SMs) blocks, at least one
+unsigned grid_blocks(uint64_t cap, unsigned per_sm) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (uint64_t)sms * per_sm;
+    return (unsigned)std::max<uint64_t>(1, std::min(cap, want));
 }
 
 unsigned grid_stride_blocks(uint64_t work) {
@@ -870,7 +1125,8 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
         // on) the run count of the in-place fix-up
         uint32_t* long_count = reinterpret_cast<uint32_t*>(base + L.off_flag + 4);
         unsigned long long* nruns = reinterpret_cast<unsigned long long*>(base + L.off_flag + 8);
-        if (cudaMemsetAsync(flag, 0, 16, s) != cudaSuccess) return HC_ERR_CUDA;
+        uint32_t* vlong_count = reinterpret_cast<uint32_t*>(base + L.off_flag + 16);
+        if (cudaMemsetAsync(flag, 0, 32, s) != cudaSuccess) return HC_ERR_CUDA;
         if (in_place) {
             if (cw != p.out_hi) return HC_ERR_STATE;
             // both position buffers are free once the last pass has run: at
@@ -878,15 +1134,20 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             uint64_t* run_pos = reinterpret_cast<uint64_t*>(pa);
             uint32_t* run_seg = pb;
             uint4* long_list = reinterpret_cast<uint4*>(base + L.off_long);
-            find_runs_kernel<<<L.ntiles, kFindWarps * 32, 0, s>>>(p.out_hi, 8 * skip, L.nseg, segs,
-                                                                run_pos, run_seg, nruns);
+            find_runs_kernel<<<L.ntiles, kFindWarps * 32, 0, s>>>(
+                p.out_hi, p.out_ids, 8 * skip, L.nseg, segs, run_pos, run_seg, nruns);
             sort_runs_kernel<<<grid_stride_blocks(L.total / 64), 256, 0, s>>>(
                 p.out_hi, p.out_ids, 8 * skip, p.rows, segs, run_pos, run_seg, nruns, long_list,
                 long_count, (uint32_t)(L.total / (kMaxRun + 1) + 1));
+            uint4* vlong_list = reinterpret_cast<uint4*>(base + L.off_vlong);
+            sort_mid_runs_kernel<<<grid_blocks(L.ntiles, 4), kMidWarps * 32, 0, s>>>(
+                p.out_hi, p.out_ids, 8 * skip, p.rows, segs, long_list, long_count, vlong_list,
+                vlong_count, (uint32_t)(L.total / (kMidRun + 1) + 1));
             // the word and position buffers are free now: scratch of the long runs
             long_run_kernel<<<std::min<uint32_t>(L.ntiles, 152), kRThreads, 0, s>>>(
-                p.out_hi, p.out_ids, wtmp, pa, pb, 8 * skip, p.rows, segs, long_list, long_count);
-            count_launches(3);
+                p.out_hi, p.out_ids, wtmp, pa, pb, 8 * skip, p.rows, segs, vlong_list,
+                vlong_count);
+            count_launches(4);
             if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
             return HC_OK;
         } else {

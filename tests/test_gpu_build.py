@@ -1,9 +1,11 @@
 """Algorithm 1's sorted lists from hc_build, against the oracle.
 
-hc_build radix-sorts the top 56 bits of every 16-coordinate key; runs of
-entries with equal 56-bit prefixes are then ordered by (key, low word, id)
-on the device: runs of up to 32 entries by one warp each, longer runs by one
-block each through global memory.  The cases below reach each of those paths
+hc_build radix-sorts the top 48 bits of every 16-coordinate key; runs of
+entries with equal 48-bit prefixes are then ordered by (key, low word, id)
+on the device: runs of up to 8 entries inside one 32-entry chunk, without two
+equal high words, by the streaming pass that finds the runs; other runs of
+up to 32 entries by one warp each; up to 256 by one warp through shared
+memory; longer runs by one block each through global memory.  The cases below reach each of those paths
 at sizes the oracle builds in seconds, and the lists must equal the oracle's
 bit for bit (keys, low words recomputed from the rows, ids).  The last case
 checks that hc_build returns without waiting for its stream.
@@ -51,7 +53,7 @@ def assert_lists_equal(hc, idx, oidx):
 @pytest.mark.parametrize("n,parts", [(600_000, 1), (900_000, 3), (3_000_000, 1)])
 def test_long_lists_bit_exact(hc, n, parts):
     """Lists of 300k to 3M entries: many sort tiles per list, ragged last
-    tiles, and the short runs of equal 56-bit prefixes such lists hold."""
+    tiles, and the short runs of equal 48-bit prefixes such lists hold."""
     db = datagen.make_db(n, 128, seed=n + parts)
     idx = hc.hc_build(dev(db), partitions=parts)
     oidx = O.build(db, curves=8, m=16, ell=parts)
@@ -78,6 +80,34 @@ def test_long_runs_sorted_on_the_device(hc):
     sync()
     assert np.array_equal(gids.cpu().numpy(), rids)
     assert np.array_equal(gdist.cpu().numpy(), O.int32_dist(rdist))
+    idx.free()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_runs_of_every_length_with_and_without_tied_high_words(hc, seed):
+    """Groups of 2 to 300 variants of one row.  Low nibbles redrawn: equal
+    high words (bit planes 7..4), different low words, so the run needs the
+    low words.  Bit 4 redrawn: equal 48-bit prefixes (planes 7..5) but
+    different high words.  Every run class of the fix-up is reached (inside a
+    chunk or across its edge, up to 8, 32, 256 records and beyond), and the
+    lists must equal the oracle's bit for bit."""
+    rng = np.random.default_rng(seed)
+    base = datagen.make_db(40_000, 128, seed=100 + seed)
+    parts = [base]
+    for size in (2, 3, 5, 8, 9, 20, 33, 100, 300):
+        for g in range(20):
+            row = base[rng.integers(0, len(base))]
+            v = np.repeat(row[None, :], size, axis=0)
+            if g % 2 == 0:
+                v = (v & 0xF0) | rng.integers(0, 16, size=v.shape, dtype=np.uint8)
+            else:
+                v = (v & 0xEF) | (rng.integers(0, 2, size=v.shape, dtype=np.uint8) << 4)
+            parts.append(v.astype(np.uint8))
+    db = np.concatenate(parts)
+    db = np.ascontiguousarray(db[rng.permutation(len(db))])
+    idx = hc.hc_build(dev(db))
+    oidx = O.build(db, curves=8, m=16)
+    assert_lists_equal(hc, idx, oidx)
     idx.free()
 
 
