@@ -446,11 +446,13 @@ constexpr int kLaneRun = 8;   // runs ordered inside find_runs: at most this lon
 // start listed for sort_runs.  A run's records are permuted among the run's
 // own positions, so the prefix at every position -- all that neighbouring
 // chunks read here -- never changes.  run_shift <= 32.
+template <int SHIFT>
 __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
-    uint64_t* __restrict__ hi, uint32_t* __restrict__ ids, int run_shift, uint32_t nseg,
+    uint64_t* __restrict__ hi, uint32_t* __restrict__ ids, uint32_t nseg,
     const SegInfo* __restrict__ segs, uint64_t* __restrict__ run_pos,
     uint32_t* __restrict__ run_seg, unsigned long long* __restrict__ nruns) {
     static_assert(kFindChunks % kFindBatch == 0, "whole batches");
+    static_assert(SHIFT > 0 && SHIFT <= 32, "low bits in a 32-bit word");
     __shared__ uint32_t masks[kFindWarps][kFindChunks];
     __shared__ uint32_t wbase[kFindWarps];
     __shared__ unsigned long long bbase;
@@ -458,10 +460,11 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
     uint32_t seg, lt, count;
     uint64_t start;
     tile_of(nseg, segs, si, seg, lt, start, count);
-    const uint64_t seg_end = si.start + si.len;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t low_mask = run_shift >= 32 ? 0xFFFFFFFFu : (1u << run_shift) - 1u;
+    constexpr uint32_t low_mask = SHIFT >= 32 ? 0xFFFFFFFFu : (1u << SHIFT) - 1u;
+    // the segment goes on before this tile / after its last record
+    const bool tile_after = lt + 1 < si.ntiles;
     uint32_t found = 0;
     for (int c0 = 0; c0 < kFindChunks; c0 += kFindBatch) {
         // a chunk's words and ids, plus the word before it (lane 0) or after
@@ -476,30 +479,29 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
             hv[j] = ok ? __ldg(hi + i) : 0;
             dv[j] = ok ? __ldg(ids + i) : 0u;
             uint64_t h = 0;
-            if (ok && lane == 0 && i > si.start) h = hi[i - 1];
-            if (ok && lane == 31 && i + 1 < seg_end) h = hi[i + 1];
+            if (ok && lane == 0 && (lt > 0 || off > 0)) h = hi[i - 1];
+            if (ok && lane == 31 && (off + 1 < count || tile_after)) h = hi[i + 1];
             halo[j] = h;
         }
 #pragma unroll
         for (int j = 0; j < kFindBatch; ++j) {
             const uint32_t base = (warp * kFindChunks + (uint32_t)(c0 + j)) * 32;
             const uint32_t off = base + (uint32_t)lane;
-            const uint64_t i = start + off;
             const bool ok = off < count;
             const uint64_t w = hv[j];
-            const uint64_t key = w >> run_shift;
             // every lane takes part in both shuffles; the end lanes then use their halo
             const uint64_t up = __shfl_up_sync(0xffffffffu, w, 1);
             const uint64_t dn = __shfl_down_sync(0xffffffffu, w, 1);
             const uint64_t prev = lane == 0 ? halo[j] : up;
             const uint64_t next = lane == 31 ? halo[j] : dn;
-            const bool ps = ok && i > si.start && (prev >> run_shift) == key;   // run goes on before
-            const bool ns = ok && i + 1 < seg_end && (next >> run_shift) == key;  // ... and after
+            // run goes on before / after this record (equal prefixes w >> SHIFT)
+            const bool ps = ok && (lt > 0 || off > 0) && ((prev ^ w) >> SHIFT) == 0;
+            const bool ns = ok && (off + 1 < count || tile_after) && ((next ^ w) >> SHIFT) == 0;
+            const uint32_t brk = __ballot_sync(0xffffffffu, !ps);
+            const uint32_t ends = __ballot_sync(0xffffffffu, !ns);
             uint32_t listed = 0;
-            if (__ballot_sync(0xffffffffu, ps || ns)) {
+            if ((brk & ends) != 0xffffffffu) {
                 // this lane's run inside the chunk: lanes s..e (cut at the chunk's edges)
-                const uint32_t brk = __ballot_sync(0xffffffffu, !ps);
-                const uint32_t ends = __ballot_sync(0xffffffffu, !ns);
                 const uint32_t below = brk & (0xFFFFFFFFu >> (31 - lane));
                 const uint32_t above = ends >> lane;
                 const bool cut = below == 0 || above == 0;   // the run crosses an edge
@@ -619,17 +621,15 @@ __device__ __forceinline__ void warp_sort_run(uint64_t* hi, uint32_t* ids, int r
     __syncwarp();
 }
 
-// The runs find_runs listed, 32 per warp at a time.  First each lane takes
-// one: a run of at most kLaneRun records without two equal high words is
-// ordered by that lane alone (its records share the prefix, so the low
-// run_shift bits order them); then the warp takes the runs its lanes left,
-// one after another (warp_sort_run).
+// The runs find_runs listed, one per lane: a run of at most kLaneRun records
+// without two equal high words is ordered by that lane alone (its records
+// share the prefix, so the low run_shift bits order them); every other run is
+// appended to `deferred` for sort_runs_warp (one atomic per warp).
 __global__ void __launch_bounds__(256) sort_runs_kernel(
-    uint64_t* hi, uint32_t* ids, int run_shift, RowKeys rows, const SegInfo* __restrict__ segs,
+    uint64_t* hi, uint32_t* ids, int run_shift, const SegInfo* __restrict__ segs,
     const uint64_t* __restrict__ run_pos, const uint32_t* __restrict__ run_seg,
-    const unsigned long long* __restrict__ nruns, uint4* __restrict__ long_list,
-    uint32_t* __restrict__ long_count, uint32_t long_cap) {
-    static_assert(kMaxRun == 32, "one run record per lane");
+    const unsigned long long* __restrict__ nruns, uint4* __restrict__ deferred,
+    uint32_t* __restrict__ deferred_count, uint32_t deferred_cap) {
     const int lane = threadIdx.x & 31;
     const uint64_t n = *nruns;
     const uint32_t low_mask = run_shift >= 32 ? 0xFFFFFFFFu : (1u << run_shift) - 1u;
@@ -687,119 +687,117 @@ __global__ void __launch_bounds__(256) sort_runs_kernel(
                 }
             }
         }
-        uint32_t todo = __ballot_sync(0xffffffffu, left);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint64_t rs2 = __shfl_sync(0xffffffffu, rs, src);
-            const uint32_t seg2 = __shfl_sync(0xffffffffu, seg, src);
-            warp_sort_run(hi, ids, run_shift, rows, segs, rs2, seg2, long_list, long_count,
-                          long_cap, lane);
+        const uint32_t todo = __ballot_sync(0xffffffffu, left);
+        if (todo) {
+            uint32_t at = 0;
+            if (lane == 0) at = atomicAdd(deferred_count, (uint32_t)__popc(todo));
+            at = __shfl_sync(0xffffffffu, at, 0) + (uint32_t)__popc(todo & ((1u << lane) - 1u));
+            if (left && HC_IN_BOUNDS(kSiteRunList, at, deferred_cap))
+                deferred[at] = make_uint4((uint32_t)rs, (uint32_t)(rs >> 32), seg, 0u);
         }
     }
 }
 
-// Runs of kMaxRun + 1 .. kMidRun records, as listed by sort_runs: one warp
-// per run (grid-stride over the list).  The warp finds the run's end, stages
-// its records in shared memory and ranks each record among them by (high
-// word, id); when two high words tie it computes every record's low word from
-// its row and ranks by (high word, low word, id).  A longer run is listed for
-// long_run_kernel.
+// The runs sort_runs deferred: one warp each (warp_sort_run).
+__global__ void __launch_bounds__(256) sort_runs_warp_kernel(
+    uint64_t* hi, uint32_t* ids, int run_shift, RowKeys rows, const SegInfo* __restrict__ segs,
+    const uint4* __restrict__ deferred, const uint32_t* __restrict__ deferred_count,
+    uint4* __restrict__ long_list, uint32_t* __restrict__ long_count, uint32_t long_cap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = *deferred_count;
+    const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += nw) {
+        const uint4 fe = deferred[r];
+        warp_sort_run(hi, ids, run_shift, rows, segs, ((uint64_t)fe.y << 32) | fe.x, fe.z,
+                      long_list, long_count, long_cap, lane);
+    }
+}
+
+// Runs of kMaxRun + 1 .. kMidRun records, as listed by sort_runs_warp: one
+// block per run (grid-stride over the list), one record per thread.  The
+// block finds the run's end, stages its records in shared memory, and each
+// thread counts the records below its own by the low run_shift bits (the
+// records share the prefix); equal low bits are equal high words, and then
+// every record's low word is computed from its row and the counts are taken
+// by (high word, low word, id).  A longer run is listed for long_run_kernel.
 constexpr uint32_t kMidRun = 256;
-constexpr int kMidWarps = 8;
 
-struct MidRunSmem {
-    uint64_t h[kMidWarps][kMidRun];
-    uint64_t l[kMidWarps][kMidRun];
-    uint32_t d[kMidWarps][kMidRun];
-};
-
-__global__ void __launch_bounds__(kMidWarps * 32) sort_mid_runs_kernel(
+__global__ void __launch_bounds__(kMidRun) sort_mid_runs_kernel(
     uint64_t* hi, uint32_t* ids, int run_shift, RowKeys rows, const SegInfo* __restrict__ segs,
     const uint4* __restrict__ long_list, const uint32_t* __restrict__ long_count,
     uint4* __restrict__ vlong_list, uint32_t* __restrict__ vlong_count, uint32_t vlong_cap) {
-    __shared__ MidRunSmem sm;
-    const int lane = threadIdx.x & 31;
-    const uint32_t warp = threadIdx.x >> 5;
-    uint64_t* sh = sm.h[warp];
-    uint64_t* sl = sm.l[warp];
-    uint32_t* sd = sm.d[warp];
+    __shared__ uint64_t sh[kMidRun];
+    __shared__ uint64_t sl[kMidRun];
+    __shared__ uint32_t sd[kMidRun];
+    __shared__ uint32_t s_n;
+    __shared__ int s_tie;
+    const uint32_t t = threadIdx.x;
+    const uint32_t low_mask = run_shift >= 32 ? 0xFFFFFFFFu : (1u << run_shift) - 1u;
     const uint32_t total = *long_count;
-    const uint32_t nw = gridDim.x * kMidWarps;
-    for (uint32_t e = blockIdx.x * kMidWarps + warp; e < total; e += nw) {
+    for (uint32_t e = blockIdx.x; e < total; e += gridDim.x) {
         const uint4 fe = long_list[e];
         const uint64_t rs = ((uint64_t)fe.y << 32) | fe.x;
         const uint32_t seg = fe.z;
         const uint64_t seg_end = segs[seg].start + segs[seg].len;
         const uint64_t pre = hi[rs] >> run_shift;
-        // the run's length, looked at 32 records at a time up to kMidRun + 1
-        uint32_t n = 0;
-        for (uint32_t b = 0;; b += 32) {
-            const uint64_t i = rs + b + (uint32_t)lane;
-            const bool in = i < seg_end && (hi[i] >> run_shift) == pre;
-            const uint32_t m = __ballot_sync(0xffffffffu, in);
-            if (m != 0xffffffffu) {
-                n = b + (uint32_t)(__ffs(~m) - 1);
-                break;
-            }
-            if (b + 32 > kMidRun) {
-                n = kMidRun + 1;
-                break;
-            }
+        if (t == 0) {
+            s_n = kMidRun + 1;
+            s_tie = 0;
         }
+        __syncthreads();
+        // the first of the next kMidRun + 1 records outside the run bounds it
+        for (uint32_t k = t; k <= kMidRun; k += blockDim.x) {
+            const uint64_t i = rs + k;
+            if (i >= seg_end || (hi[i] >> run_shift) != pre) atomicMin(&s_n, k);
+        }
+        __syncthreads();
+        const uint32_t n = s_n;
         if (n > kMidRun) {
-            if (lane == 0) {
+            if (t == 0) {
                 const uint32_t vi = atomicAdd(vlong_count, 1u);
                 if (HC_IN_BOUNDS(kSiteRunList, vi, vlong_cap)) vlong_list[vi] = fe;
             }
+            __syncthreads();
             continue;
         }
-        bool tie = false;
-        for (uint32_t i = lane; i < n; i += 32) {
-            sh[i] = hi[rs + i];
-            sd[i] = ids[rs + i];
+        uint64_t h = 0;
+        uint32_t d = 0;
+        if (t < n) {
+            h = hi[rs + t];
+            d = ids[rs + t];
+            sh[t] = h;
+            sd[t] = d;
         }
-        __syncwarp();
-        for (uint32_t i = lane; i < n; i += 32)
-            for (uint32_t j = 0; j < n; ++j) tie |= j != i && sh[j] == sh[i];
-        const bool need_lo = __any_sync(0xffffffffu, tie);
-        if (need_lo) {
-            const uint32_t curve = seg % rows.P.curves;
-            for (uint32_t i = lane; i < n; i += 32)
-                sl[i] = row_key_lo(rows.db, rows.row_bytes, rows.P, sd[i], curve);
-            __syncwarp();
+        __syncthreads();
+        uint32_t r = 0;
+        if (t < n) {
+            const uint32_t x = (uint32_t)h & low_mask;
+            bool tie = false;
+            for (uint32_t j = 0; j < n; ++j) {
+                const uint32_t y = (uint32_t)sh[j] & low_mask;
+                r += (y < x || (y == x && j < t)) ? 1u : 0u;
+                tie |= y == x && j != t;
+            }
+            if (tie) s_tie = 1;
         }
-        uint32_t rk[kMidRun / 32];
-#pragma unroll
-        for (int t = 0; t < (int)(kMidRun / 32); ++t) {
-            const uint32_t i = (uint32_t)lane + 32u * (uint32_t)t;
-            uint32_t r = 0;
-            if (i < n) {
-                const uint64_t hx = sh[i];
-                const uint32_t dx = sd[i];
-                const uint64_t lx = need_lo ? sl[i] : 0;
+        __syncthreads();
+        if (s_tie) {
+            if (t < n) sl[t] = row_key_lo(rows.db, rows.row_bytes, rows.P, d, seg % rows.P.curves);
+            __syncthreads();
+            if (t < n) {
+                const uint64_t lx = sl[t];
+                r = 0;
                 for (uint32_t j = 0; j < n; ++j) {
-                    const uint64_t hj = sh[j];
-                    bool before = hj < hx;
-                    if (hj == hx) {
-                        const uint64_t lj = need_lo ? sl[j] : 0;
-                        before = lj < lx || (lj == lx && sd[j] < dx);
-                    }
-                    r += before ? 1u : 0u;
+                    const uint64_t hj = sh[j], lj = sl[j];
+                    r += (hj < h || (hj == h && (lj < lx || (lj == lx && sd[j] < d)))) ? 1u : 0u;
                 }
             }
-            rk[t] = r;
         }
-        __syncwarp();
-#pragma unroll
-        for (int t = 0; t < (int)(kMidRun / 32); ++t) {
-            const uint32_t i = (uint32_t)lane + 32u * (uint32_t)t;
-            if (i < n && HC_IN_BOUNDS(kSiteRunWrite, rk[t], n)) {
-                hi[rs + rk[t]] = sh[i];
-                ids[rs + rk[t]] = sd[i];
-            }
+        if (t < n && HC_IN_BOUNDS(kSiteRunWrite, r, n)) {
+            hi[rs + r] = h;
+            ids[rs + r] = d;
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -992,7 +990,7 @@ Layout make_layout(const SortProblem& p) {
     L.off_counts = o;  o = align_up(o + sizeof(uint32_t) * (L.ncounts ? L.ncounts : 1));
     L.off_totals = o;  o = align_up(o + sizeof(uint32_t) * 256 * (L.nseg ? L.nseg : 1));
     L.off_segs = o;    o = align_up(o + sizeof(SegInfo) * (L.nseg ? L.nseg : 1));
-    L.off_flag = o;    o = align_up(o + 32);   // flag, long count (+4), run count (+8), very long count (+16)
+    L.off_flag = o;    o = align_up(o + 32);   // flag; counts of long runs (+4), runs (+8), very long runs (+16), deferred runs (+20)
     L.off_digits = o;  o = align_up(o + L.total);
     // runs longer than kMaxRun: at most total / (kMaxRun + 1) of them
     L.off_long = o;    o = align_up(o + sizeof(uint4) * (L.total / (kMaxRun + 1) + 1));
@@ -1134,20 +1132,35 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             uint64_t* run_pos = reinterpret_cast<uint64_t*>(pa);
             uint32_t* run_seg = pb;
             uint4* long_list = reinterpret_cast<uint4*>(base + L.off_long);
-            find_runs_kernel<<<L.ntiles, kFindWarps * 32, 0, s>>>(
-                p.out_hi, p.out_ids, 8 * skip, L.nseg, segs, run_pos, run_seg, nruns);
+            switch (skip) {
+#define HC_FIND(K)                                                                          \
+    case K:                                                                                 \
+        find_runs_kernel<8 * K><<<L.ntiles, kFindWarps * 32, 0, s>>>(                       \
+            p.out_hi, p.out_ids, L.nseg, segs, run_pos, run_seg, nruns);                    \
+        break;
+                HC_FIND(1) HC_FIND(2) HC_FIND(3) HC_FIND(4)
+#undef HC_FIND
+                default: return HC_ERR_STATE;   // prefixes of at least 32 bits are sorted
+            }
+            // the word buffer is free after the last pass: the list of runs the
+            // lanes leave to warps (at most total / 2 entries of 16 bytes)
+            uint4* deferred = reinterpret_cast<uint4*>(wtmp);
+            uint32_t* deferred_count = reinterpret_cast<uint32_t*>(base + L.off_flag + 20);
             sort_runs_kernel<<<grid_stride_blocks(L.total / 64), 256, 0, s>>>(
-                p.out_hi, p.out_ids, 8 * skip, p.rows, segs, run_pos, run_seg, nruns, long_list,
+                p.out_hi, p.out_ids, 8 * skip, segs, run_pos, run_seg, nruns, deferred,
+                deferred_count, (uint32_t)(L.total / 2));
+            sort_runs_warp_kernel<<<grid_blocks(L.ntiles, 8), 256, 0, s>>>(
+                p.out_hi, p.out_ids, 8 * skip, p.rows, segs, deferred, deferred_count, long_list,
                 long_count, (uint32_t)(L.total / (kMaxRun + 1) + 1));
             uint4* vlong_list = reinterpret_cast<uint4*>(base + L.off_vlong);
-            sort_mid_runs_kernel<<<grid_blocks(L.ntiles, 4), kMidWarps * 32, 0, s>>>(
+            sort_mid_runs_kernel<<<grid_blocks(L.ntiles, 8), kMidRun, 0, s>>>(
                 p.out_hi, p.out_ids, 8 * skip, p.rows, segs, long_list, long_count, vlong_list,
                 vlong_count, (uint32_t)(L.total / (kMidRun + 1) + 1));
             // the word and position buffers are free now: scratch of the long runs
             long_run_kernel<<<std::min<uint32_t>(L.ntiles, 152), kRThreads, 0, s>>>(
                 p.out_hi, p.out_ids, wtmp, pa, pb, 8 * skip, p.rows, segs, vlong_list,
                 vlong_count);
-            count_launches(4);
+            count_launches(5);
             if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
             return HC_OK;
         } else {
