@@ -160,7 +160,7 @@ HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, u
 
 /*
  * hc_query_ordered -- hc_query with the queries answered in the order of
- * their curve-0 extended-keys (the top 32 key bits, radix-sorted on the
+ * their curve-0 extended-keys (the top 16 key bits, radix-sorted on the
  * device), so that queries answered at the same time read overlapping
  * windows and share their rows in L2.  The paper batches queries in arrival
  * order (Sec. 5.1); the order changes no result: every query's ids and

@@ -490,7 +490,7 @@ constexpr uint32_t kHostOrderedMin = 4096;
 SortProblem order_problem(uint32_t nq) {
     SortProblem sp;
     sp.seg_off = {0, (uint64_t)nq};
-    sp.key_bits = 32;
+    sp.key_bits = kOrderBits;
     sp.allow_sync = false;   // no stream wait: every key byte is sorted
     return sp;
 }
@@ -523,7 +523,7 @@ int enqueue_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, u
     if (rc) return rc;
     SortProblem sp = order_problem(nq);
     sp.seg_off_dev = seg;
-    sp.hi = keys;   // gathered along, not compared (key_bits = 32)
+    sp.hi = keys;   // gathered along, not compared (key_bits <= 64)
     sp.lo = keys;
     sp.ids = nullptr;
     sp.id_base_dev = seg + 2;   // ids = positions 0..nq-1

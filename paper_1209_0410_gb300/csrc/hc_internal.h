@@ -111,7 +111,10 @@ cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32
                          int32_t* out_ids, void* out_dist, cudaStream_t s,
                          const uint32_t* p_query = nullptr, const int64_t* pos_in = nullptr,
                          const uint32_t* order = nullptr);
-// The top 32 bits of each query's curve-0 extended-key, as the low word of a
+// Bits of the curve-0 key that order a batch in hc_query_ordered: 65,536
+// buckets keep a batch's neighbouring queries together at two radix passes.
+constexpr uint32_t kOrderBits = 16;
+// The top kOrderBits bits of each query's curve-0 extended-key, as the low word of a
 // sort key (the order in which hc_query_ordered answers the queries).
 cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, uint64_t* keys,
                               cudaStream_t s);

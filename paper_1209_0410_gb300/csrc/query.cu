@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kerne
                             static_cast<uint32_t*>(a.out_dist) + (size_t)qi * a.k);
 }
 
-// keys[i] = top 32 bits of query i's curve-0 extended-key (one thread each)
+// keys[i] = top kOrderBits bits of query i's curve-0 extended-key (one thread each)
 __global__ void __launch_bounds__(256) order_keys_kernel(IndexView ix, const uint8_t* q,
                                                          uint32_t nq, uint64_t* keys) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) order_keys_kernel(IndexView ix, const uin
     const uint32_t bits = 8 * ix.P.m;   // key bits, right-aligned in (h, l)
     const uint64_t top = bits > 64 ? (h << (128 - bits)) | (bits < 128 ? l >> (bits - 64) : 0)
                                    : l << (64 - bits);
-    keys[i] = top >> 32;
+    keys[i] = top >> (64 - kOrderBits);
 }
 
 __global__ void __launch_bounds__(kQWarps * 32) positions_kernel(QueryArgs a) {
