@@ -18,6 +18,9 @@ from . import hc
 WPQ_CHOICES = (1, 2, 4, 8)
 BLOCK_CHOICES = ({"warps_per_block": 8, "blocks_per_sm": 2, "tile": 1},
                  {"warps_per_block": 8, "blocks_per_sm": 2, "tile": 2},
+                 {"warps_per_block": 8, "blocks_per_sm": 3, "tile": 1},
+                 {"warps_per_block": 8, "blocks_per_sm": 3, "tile": 2},
+                 {"warps_per_block": 8, "blocks_per_sm": 3, "tile": 4},
                  {"warps_per_block": 8, "blocks_per_sm": 4, "tile": 2},
                  {"warps_per_block": 4, "blocks_per_sm": 4, "tile": 2},
                  {"warps_per_block": 16, "blocks_per_sm": 1, "tile": 1},

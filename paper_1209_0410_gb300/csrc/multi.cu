@@ -64,7 +64,8 @@ uint32_t variant_of(hc_dtype t, uint32_t row_bytes, uint32_t k) {
 // rows of at most 128 bytes, else null.
 template <bool F32, int LPR, int KR>
 __device__ void multi_query(const MultiJob& J, uint32_t qi, bool active, uint32_t sub,
-                            uint32_t* pos_w, uint64_t* group_buf, uint8_t* ring, int lane) {
+                            uint32_t* pos_w, uint32_t lists_cap, uint64_t* group_buf,
+                            uint8_t* ring, int lane) {
     WarpTopK<KR> top;
     top.init();
     if (active && !HC_IN_BOUNDS(kSiteMultiQuery, qi, J.nq)) active = false;
@@ -73,13 +74,21 @@ __device__ void multi_query(const MultiJob& J, uint32_t qi, bool active, uint32_
         if constexpr (LPR <= 8) {
             if (ring && J.ix.row_bytes <= 128) {
                 search_lists_staged<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w,
-                                                  pos_w + kMaxLists, ring, top, lane);
+                                                  pos_w + lists_cap, ring, top, lane);
             } else {
                 search_lists<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w, top, lane);
             }
         } else {
             search_lists<F32, LPR, KR>(J.ix, qrow, J.p, J.k, sub, J.wpq, pos_w, top, lane);
         }
+    }
+    // one warp per query (the same for every warp of the block: one job per
+    // task): the warp's list is the query's, written without a block barrier
+    if (J.wpq == 1) {
+        if (active)
+            top.template store<F32>(J.k, lane, J.ids + (size_t)qi * J.k,
+                                    static_cast<uint32_t*>(J.dist) + (size_t)qi * J.k);
+        return;
     }
     // every warp publishes its list; the group leader folds the others in
     uint64_t* mine = group_buf + (size_t)sub * 4 * 32;
@@ -100,24 +109,26 @@ __device__ void multi_query(const MultiJob& J, uint32_t qi, bool active, uint32_
 
 template <int V>
 __device__ __forceinline__ void run_variant(const MultiJob& J, uint32_t qi, bool active,
-                                            uint32_t sub, uint32_t* pos_w, uint64_t* mb,
-                                            uint8_t* ring, int lane) {
+                                            uint32_t sub, uint32_t* pos_w, uint32_t lists_cap,
+                                            uint64_t* mb, uint8_t* ring, int lane) {
     constexpr int CLS = V / 2;
     constexpr bool F32 = CLS >= 3;
     constexpr int LPR = CLS == 0 ? 4 : (CLS == 1 ? 8 : (CLS == 2 ? 16 : (CLS == 3 ? 16 : 32)));
     constexpr int KR = (V & 1) ? 4 : 1;
-    multi_query<F32, LPR, KR>(J, qi, active, sub, pos_w, mb, ring, lane);
+    multi_query<F32, LPR, KR>(J, qi, active, sub, pos_w, lists_cap, mb, ring, lane);
 }
 
 __global__ void __launch_bounds__(kMaxWarps * 32)
     multi_kernel(const MultiJob* __restrict__ jobs, const MultiTask* __restrict__ tasks,
-                 uint32_t ntasks, uint32_t tile, uint32_t* __restrict__ counter, bool staged) {
+                 uint32_t ntasks, uint32_t tile, uint32_t* __restrict__ counter, bool staged,
+                 uint32_t lists_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t nwarps = blockDim.x >> 5;
     uint64_t* merge = reinterpret_cast<uint64_t*>(smem_raw);             // nwarps x 4 x 32
-    // per warp: kMaxLists positions, then kMaxLists window prefixes
+    // per warp: lists_cap positions, then lists_cap window prefixes (lists_cap:
+    // the plan's largest index, a multiple of 4, so the rings stay 16-byte aligned)
     uint32_t* pos = reinterpret_cast<uint32_t*>(merge + nwarps * 4 * 32);
-    uint8_t* rings = reinterpret_cast<uint8_t*>(pos + nwarps * 2 * kMaxLists); // nwarps x kRingBytes
+    uint8_t* rings = reinterpret_cast<uint8_t*>(pos + nwarps * 2 * lists_cap); // nwarps x kRingBytes
     __shared__ uint32_t s_task;
     const int lane = threadIdx.x & 31;
     const uint32_t warp = threadIdx.x >> 5;
@@ -129,7 +140,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
         if (t >= ntasks) return;
         const MultiTask T = tasks[t];
         const MultiJob& J = jobs[T.job];
-        if (!HC_IN_BOUNDS(kSiteMultiLists, J.ix.lists, kMaxLists + 1)) continue;
+        if (!HC_IN_BOUNDS(kSiteMultiLists, J.ix.lists, lists_cap + 1)) continue;
         const uint32_t group = warp / J.wpq, sub = warp % J.wpq;
         const uint32_t per_pass = nwarps / J.wpq;
         uint64_t* mb = merge + (size_t)(group * J.wpq) * 4 * 32;
@@ -137,11 +148,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
             const uint32_t qo = rep * per_pass + group;
             const bool active = group < per_pass && qo < T.cnt;
             const uint32_t qi = T.q0 + qo;
-            uint32_t* pw = pos + (size_t)warp * 2 * kMaxLists;
+            uint32_t* pw = pos + (size_t)warp * 2 * lists_cap;
             uint8_t* ring = staged ? rings + (size_t)warp * kRingBytes : nullptr;
             switch (J.variant) {
 #define HC_V(n) \
-    case n: run_variant<n>(J, qi, active, sub, pw, mb, ring, lane); break;
+    case n: run_variant<n>(J, qi, active, sub, pw, lists_cap, mb, ring, lane); break;
                 HC_V(0) HC_V(1) HC_V(2) HC_V(3) HC_V(4) HC_V(5) HC_V(6) HC_V(7) HC_V(8)
                 HC_V(9)
 #undef HC_V
@@ -154,9 +165,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32)
 
 __global__ void reset_counter_kernel(uint32_t* c) { *c = 0; }
 
-size_t multi_smem(uint32_t nwarps, bool staged) {
+size_t multi_smem(uint32_t nwarps, bool staged, uint32_t lists_cap) {
     return (size_t)nwarps * 4 * 32 * sizeof(uint64_t) +
-           (size_t)nwarps * 2 * kMaxLists * sizeof(uint32_t) + (staged ? nwarps * kRingBytes : 0);
+           (size_t)nwarps * 2 * lists_cap * sizeof(uint32_t) + (staged ? nwarps * kRingBytes : 0);
 }
 
 }  // namespace
@@ -170,6 +181,7 @@ struct hc_multi_plan {
     unsigned grid = 0;
     size_t smem = 0;
     bool staged = false;   // some job has rows of at most 128 bytes and <= 8 lanes per row
+    uint32_t lists_cap = 4;   // largest number of lists of a job's index, rounded up to 4
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -189,7 +201,7 @@ bool on_device(const void* p) {
 int enqueue(hc_multi_plan* P, cudaStream_t s) {
     reset_counter_kernel<<<1, 1, 0, s>>>(P->counter);
     multi_kernel<<<P->grid, P->cfg.warps_per_block * 32, P->smem, s>>>(
-        P->jobs_dev, P->tasks_dev, P->ntasks, P->cfg.tile, P->counter, P->staged);
+        P->jobs_dev, P->tasks_dev, P->ntasks, P->cfg.tile, P->counter, P->staged, P->lists_cap);
     count_launches(2);
     return cudaGetLastError() == cudaSuccess ? HC_OK : HC_ERR_CUDA;
 }
@@ -289,8 +301,11 @@ HC_API int hc_multi_plan_create(const hc_multi_job* jobs, uint32_t njobs,
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (const MultiJob& j : hj) P->staged |= j.variant / 2 <= 1;   // uint8 rows <= 128 bytes
-    P->smem = multi_smem(cfg.warps_per_block, P->staged);
+    for (const MultiJob& j : hj) {
+        P->staged |= j.variant / 2 <= 1;   // uint8 rows <= 128 bytes
+        P->lists_cap = std::max(P->lists_cap, (j.ix.lists + 3u) & ~3u);
+    }
+    P->smem = multi_smem(cfg.warps_per_block, P->staged, P->lists_cap);
     if (cudaFuncSetAttribute(multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)P->smem) != cudaSuccess) {
         free_plan(P);
