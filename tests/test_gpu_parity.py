@@ -272,11 +272,11 @@ def test_duplicate_rows_rank_lower_id_first(hc):
 
 @pytest.mark.parametrize("parts,copies", [(1, 40), (3, 40), (1, 32), (1, 33), (2, 31)])
 def test_build_long_runs_of_equal_keys(hc, parts, copies):
-    """Rows repeated `copies` times: runs of equal keys up to 32 are ordered
-    by the in-place fix-up (ties of the high word read low words from the
-    rows); longer runs make the build compute the low words and sort by every
-    key byte.  The lists (low words recomputed from the rows) and queries
-    (which tie on the high word) match the oracle either way."""
+    """Rows repeated `copies` times: runs of equal keys (equal high words,
+    so the low words are read from the rows) of up to 32 entries are ordered
+    by one warp each, longer ones by one block each.  The lists (low words
+    recomputed from the rows) and queries (which tie on the high word) match
+    the oracle."""
     rng = np.random.default_rng(17)
     base = rng.integers(0, 256, size=(60, 128), dtype=np.uint8)
     db = np.concatenate([np.repeat(base, copies, axis=0),
