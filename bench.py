@@ -234,7 +234,7 @@ def build_bytes(n, row_bytes, curves, passes=BUILD_PASSES):
     out plus the next pass's digit byte; the last pass writes ids in place of
     positions and no digit); then the run fix-up's read of the high words and
     ids (it reorders the short runs in place; the few records it moves are
-    not counted)."""
+    not counted) and its write of the search fence (every 16th high word)."""
     r = curves * n
     algorithmic = n * row_bytes + r * 20 + passes * 2 * r * 20
     counts = 4 * 4 * 256 * (r / 4096.0)
@@ -245,6 +245,7 @@ def build_bytes(n, row_bytes, curves, passes=BUILD_PASSES):
         kernel += r * (8 if first else 12)              # scatter reads
         kernel += r * (12 if last else 13)              # scatter writes
     kernel += r * 12                                    # run fix-up
+    kernel += r * 0.5                                   # fence: 8 B per 16 entries
     return float(algorithmic), float(kernel)
 
 
@@ -397,14 +398,17 @@ def run_hc(a):
         if world > 1:
             dist.barrier()
 
-    workspace = torch.empty(hc.hc_query_ordered_workspace(a.nq), dtype=torch.uint8,
-                            device="cuda")
+    workspace = []   # sized by the first index (every step's index has the same lists)
+
     def query(idx, p=None):
         if a.input_order:
             hc.hc_query(idx, q, a.k, a.p if p is None else p, out_ids, out_dist, stream=stream)
         else:
+            if not workspace:
+                workspace.append(torch.empty(hc.hc_query_ordered_workspace(idx, a.nq),
+                                             dtype=torch.uint8, device="cuda"))
             hc.hc_query_ordered(idx, q, a.k, a.p if p is None else p, out_ids, out_dist,
-                                workspace=workspace, stream=stream)
+                                workspace=workspace[0], stream=stream)
 
     def step(ev):
         ev[0].record(stream)
@@ -461,7 +465,9 @@ def run_hc(a):
     if (a.n_db, a.nq, a.p, a.k, a.dtype, a.input_order) != (10_000_000, 100_000, 128, 10, "u8",
                                                             False):
         traffic = None
-    roofline = {"kernel": "query_kernel (fused K1+K3+K4+K5+K6)", "bound": "hbm",
+    roofline = {"kernel": "hc_query_ordered: order keys + sort + batch lower_bound (K1, K3) "
+                          "+ query_kernel walk (K4..K6); time of the whole call",
+                "bound": "hbm",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": traffic,

@@ -367,7 +367,7 @@ def run_serve(a):
     qb = torch.from_numpy(np.ascontiguousarray(pool[:100_000])).cuda()
     ob_ids = torch.empty((qb.shape[0], 10), dtype=torch.int32, device="cuda")
     ob_dist = torch.empty((qb.shape[0], 10), dtype=torch.int32, device="cuda")
-    ws = torch.empty(hc.hc_query_ordered_workspace(qb.shape[0]), dtype=torch.uint8,
+    ws = torch.empty(hc.hc_query_ordered_workspace(idx, qb.shape[0]), dtype=torch.uint8,
                      device="cuda")
     hc.hc_query_ordered(idx, qb, 10, 128, ob_ids, ob_dist, workspace=ws)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]

@@ -162,16 +162,23 @@ HC_API int hc_query(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, u
  * hc_query_ordered -- hc_query with the queries answered in the order of
  * their curve-0 extended-keys (the top 16 key bits, radix-sorted on the
  * device), so that queries answered at the same time read overlapping
- * windows and share their rows in L2.  The paper batches queries in arrival
- * order (Sec. 5.1); the order changes no result: every query's ids and
- * distances land in its own row and equal those of hc_query.
- *   workspace_dev    device memory of at least hc_query_ordered_workspace(nq)
- *                    bytes, 256-byte aligned, owned by the caller (contents
- *                    scratch; one call at a time per workspace)
+ * windows and share their rows in L2.  The batch is also sorted by every
+ * other curve's key, and the lower_bound of every query in every list
+ * (Algorithm 2's search) runs first as one pass over the batch, 32
+ * neighbouring keys of one curve per warp, into the workspace; the walk then
+ * reads those positions.  The paper batches
+ * queries in arrival order (Sec. 5.1); the order changes no result: every
+ * query's ids and distances land in its own row and equal those of hc_query.
+ *   workspace_dev    device memory of at least
+ *                    hc_query_ordered_workspace(idx, nq) bytes (it depends on
+ *                    the index's curves and lists, not on its rows), 256-byte
+ *                    aligned, owned by the caller (contents scratch; one call
+ *                    at a time per workspace)
  * Other arguments as hc_query.  No allocation; asynchronous on cuda_stream.
  * HC_ERR_ARG if the workspace is missing, misaligned or too small.
+ * hc_query_ordered_workspace returns 0 for idx = NULL or nq = 0.
  */
-HC_API size_t hc_query_ordered_workspace(uint32_t nq);
+HC_API size_t hc_query_ordered_workspace(const hc_index* idx, uint32_t nq);
 HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
                             int32_t* out_ids_dev, void* out_dist_dev, void* workspace_dev,
                             size_t workspace_bytes, void* cuda_stream);

@@ -191,6 +191,7 @@ void index_destroy(hc_index* x, cudaStream_t s) {
     pool_free(x->keys_hi, s);
     pool_free(x->keys_lo, s);
     pool_free(x->ids, s);
+    pool_free(x->fence, s);
     pool_free(x->list_off_dev, s);
     pool_free(x->st_q, s);
     pool_free(x->st_out, s);
@@ -234,6 +235,9 @@ int index_alloc(hc_index* x, cudaStream_t s) {
     if ((rc = dev_alloc_async((void**)&x->keys_hi, sizeof(uint64_t) * total, s))) return rc;
     if (index_keeps_lo(x->params) &&
         (rc = dev_alloc_async((void**)&x->keys_lo, sizeof(uint64_t) * total, s)))
+        return rc;
+    if (total > 0 && (rc = dev_alloc_async((void**)&x->fence,
+                                           sizeof(uint64_t) * ((total + 15) >> kFenceShift), s)))
         return rc;
     return dev_alloc_async((void**)&x->ids, sizeof(uint32_t) * total, s);
 }
@@ -291,6 +295,7 @@ int build_index(hc_index* x, cudaStream_t s) {
     sp.out_hi = x->keys_hi;
     sp.out_lo = x->keys_lo;
     sp.out_ids = x->ids;
+    sp.out_fence = x->fence;
     const size_t sort_bytes = sort_scratch_bytes(sp);
     const size_t key_bytes = ((sizeof(uint64_t) * (keep_lo ? 2 : 1) * total) + 255) & ~(size_t)255;
     const size_t base_bytes = (sizeof(uint64_t) * x->lists + 255) & ~(size_t)255;
@@ -476,10 +481,14 @@ HC_API int hc_query_at(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k
 
 namespace {
 
-// Workspace of hc_query_ordered for nq queries: sort keys, the segment table,
-// the sorted keys and the permutation, then the sort's own scratch.
+// Workspace of hc_query_ordered for nq queries: the order keys of every
+// curve, the segment table (a segment per curve, at most 32: one small
+// upload), the sorted keys and the permutations (curve 0's first: the walk
+// order), the query keys and the positions of the batch search, then the
+// sort's own scratch.
 struct OrderLayout {
-    size_t keys = 0, seg = 0, out_hi = 0, out_lo = 0, order = 0, sort = 0, bytes = 0;
+    size_t keys = 0, seg = 0, out_hi = 0, out_lo = 0, order = 0, qhi = 0, qlo = 0, pos = 0,
+           sort = 0, bytes = 0;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -487,46 +496,57 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // hc_query_host answers batches of at least this many queries in key order
 constexpr uint32_t kHostOrderedMin = 4096;
 
-SortProblem order_problem(uint32_t nq) {
+// one segment of nq order keys per sorted curve
+SortProblem order_problem(uint32_t nq, uint32_t ncurves) {
     SortProblem sp;
-    sp.seg_off = {0, (uint64_t)nq};
+    sp.seg_off.resize(ncurves + 1);
+    for (uint32_t c = 0; c <= ncurves; ++c) sp.seg_off[c] = (uint64_t)c * nq;
     sp.key_bits = kOrderBits;
     sp.allow_sync = false;   // no stream wait: every key byte is sorted
     return sp;
 }
 
-OrderLayout order_layout(uint32_t nq) {
+OrderLayout order_layout(const hc_index* idx, uint32_t nq) {
     OrderLayout L;
+    const uint32_t curves = idx->params.curves;
+    const uint64_t r = (uint64_t)nq * curves;
     size_t o = 0;
-    L.keys = o;    o = align256(o + 8ull * nq);
-    L.seg = o;     o = align256(o + 8 * 3);      // seg_off[2], id_base[1]
-    L.out_hi = o;  o = align256(o + 8ull * nq);
-    L.out_lo = o;  o = align256(o + 8ull * nq);
-    L.order = o;   o = align256(o + 4ull * nq);
-    L.sort = o;    o = align256(o + sort_scratch_bytes(order_problem(nq)));
+    L.keys = o;    o = align256(o + 8 * r);
+    L.seg = o;     o = align256(o + 8 * (2 * curves + 1));   // seg_off, then id_base
+    L.out_hi = o;  o = align256(o + 8 * r);
+    L.out_lo = o;  o = align256(o + 8 * r);
+    L.order = o;   o = align256(o + 4 * r);
+    L.qhi = o;     o = align256(o + 8 * r);
+    L.qlo = o;     o = align256(o + 8 * r);
+    L.pos = o;     o = align256(o + 4ull * nq * idx->lists);
+    L.sort = o;    o = align256(o + sort_scratch_bytes(order_problem(nq, curves)));
     L.bytes = o;
     return L;
 }
 
-
-// hc_query_ordered's work on a checked workspace of order_layout(nq).bytes:
-// the curve-0 order keys, their sort, then the walk in that order.
+// hc_query_ordered's work on a checked workspace of order_layout(idx, nq).bytes:
+// the order keys, their sort, the batch search, then the walk in curve-0 order.
 int enqueue_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
                     int32_t* out_ids_dev, void* out_dist_dev, char* ws, cudaStream_t s) {
-    const OrderLayout L = order_layout(nq);
+    const OrderLayout L = order_layout(idx, nq);
+    const uint32_t curves = idx->params.curves;
     uint64_t* keys = reinterpret_cast<uint64_t*>(ws + L.keys);
     uint64_t* seg = reinterpret_cast<uint64_t*>(ws + L.seg);
+    uint64_t* qhi = reinterpret_cast<uint64_t*>(ws + L.qhi);
+    uint64_t* qlo = reinterpret_cast<uint64_t*>(ws + L.qlo);
+    uint32_t* pos = reinterpret_cast<uint32_t*>(ws + L.pos);
     const IndexView v = view_of(idx);
-    int rc = status_of(launch_order_keys(v, q_dev, nq, keys, s));
-    const uint64_t small[3] = {0, (uint64_t)nq, 0};   // seg_off, then id_base
-    if (!rc) rc = status_of(upload_small(seg, small, sizeof(small), s));
+    int rc = status_of(launch_order_keys(v, q_dev, nq, curves, keys, qhi, qlo, s));
+    std::vector<uint64_t> small(2 * curves + 1, 0);   // seg_off, then id_base = 0
+    for (uint32_t c = 0; c <= curves; ++c) small[c] = (uint64_t)c * nq;
+    if (!rc) rc = status_of(upload_small(seg, small.data(), 8 * small.size(), s));
     if (rc) return rc;
-    SortProblem sp = order_problem(nq);
+    SortProblem sp = order_problem(nq, curves);
     sp.seg_off_dev = seg;
     sp.hi = keys;   // gathered along, not compared (key_bits <= 64)
     sp.lo = keys;
     sp.ids = nullptr;
-    sp.id_base_dev = seg + 2;   // ids = positions 0..nq-1
+    sp.id_base_dev = seg + curves + 1;   // ids = ranks 0..nq-1 in every segment
     sp.out_hi = reinterpret_cast<uint64_t*>(ws + L.out_hi);
     sp.out_lo = reinterpret_cast<uint64_t*>(ws + L.out_lo);
     sp.out_ids = reinterpret_cast<uint32_t*>(ws + L.order);
@@ -534,9 +554,14 @@ int enqueue_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, u
         TraceRange to("order");
         if ((rc = sort_segments(sp, ws + L.sort, s))) return rc;
     }
+    {
+        TraceRange tb("search");
+        if ((rc = status_of(launch_batch_positions(v, nq, sp.out_ids, qhi, qlo, pos, s))))
+            return rc;
+    }
     TraceRange tq("walk");
     return status_of(launch_query(v, q_dev, nq, k, p, out_ids_dev, out_dist_dev, s, nullptr,
-                                  nullptr, sp.out_ids));
+                                  nullptr, sp.out_ids, pos));
 }
 
 // hc_query_host's work: the queries up on cs (into the index's staging), the
@@ -552,7 +577,7 @@ int enqueue_host_query(hc_index* idx, const void* q_host, uint32_t nq, uint32_t 
     // same results, fewer DRAM reads); its workspace follows the queries
     const bool ordered = nq >= kHostOrderedMin;
     const size_t ws_off = align256(qbytes);
-    const size_t st_bytes = ordered ? ws_off + order_layout(nq).bytes : qbytes;
+    const size_t st_bytes = ordered ? ws_off + order_layout(idx, nq).bytes : qbytes;
     int rc;
     if (!idx->st_done &&
         (rc = status_of(cudaEventCreateWithFlags(&idx->st_done, cudaEventDisableTiming))))
@@ -603,7 +628,9 @@ int enqueue_host_query(hc_index* idx, const void* q_host, uint32_t nq, uint32_t 
 
 extern "C" {
 
-HC_API size_t hc_query_ordered_workspace(uint32_t nq) { return nq ? order_layout(nq).bytes : 0; }
+HC_API size_t hc_query_ordered_workspace(const hc_index* idx, uint32_t nq) {
+    return idx && nq ? order_layout(idx, nq).bytes : 0;
+}
 
 HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, uint32_t p,
                             int32_t* out_ids_dev, void* out_dist_dev, void* workspace_dev,
@@ -614,7 +641,7 @@ HC_API int hc_query_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint3
     if (!q_dev || !out_ids_dev || !out_dist_dev || !aligned16(q_dev) || !workspace_dev ||
         ((uintptr_t)workspace_dev & 255))
         return HC_ERR_ARG;
-    const OrderLayout L = order_layout(nq);
+    const OrderLayout L = order_layout(idx, nq);
     if (workspace_bytes < L.bytes) return HC_ERR_ARG;
     if (!is_device_ptr(q_dev) || !is_device_ptr(out_ids_dev) || !is_device_ptr(out_dist_dev) ||
         !is_device_ptr(workspace_dev))

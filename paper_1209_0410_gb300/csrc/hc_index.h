@@ -15,6 +15,7 @@ struct hc_index {
     uint64_t* keys_hi = nullptr;
     uint64_t* keys_lo = nullptr;
     uint32_t* ids = nullptr;
+    uint64_t* fence = nullptr;       // every 16th high word (IndexView::fence)
     uint64_t* list_off_dev = nullptr;
     std::vector<uint64_t> list_off;
     uint32_t lists = 0, row_bytes = 0;
@@ -40,6 +41,8 @@ inline IndexView view_of(const hc_index* x) {
     v.keys_lo = x->keys_lo;
     v.ids = x->ids;
     v.rows = x->params.n;
+    v.fence = x->fence;
+    v.fence_len = x->fence && !x->list_off.empty() ? (x->list_off.back() + 15) >> kFenceShift : 0;
     return v;
 }
 

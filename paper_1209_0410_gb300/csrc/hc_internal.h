@@ -74,6 +74,11 @@ struct SortProblem {
     uint64_t* out_hi = nullptr;   // device, total records (distinct from sources)
     uint64_t* out_lo = nullptr;
     uint32_t* out_ids = nullptr;
+    // nullable: out_fence[j] = out_hi[16 j] & kFenceMask for j < ceil(seg_off
+    // back / 16), written by the run fix-up's first kernel on the high-word-
+    // first path (the bits of the high word the radix passes leave final),
+    // else by a pass over out_hi after the sort
+    uint64_t* out_fence = nullptr;
 };
 // Scratch bytes the sort needs for this problem (queried before allocating).
 size_t sort_scratch_bytes(const SortProblem& p);
@@ -98,7 +103,25 @@ struct IndexView {
     const uint64_t* keys_lo;   // null: low words recomputed from the rows (16-coordinate keys)
     const uint32_t* ids;
     uint64_t rows;             // database rows (bound of the row ids)
+    // fence[j] = keys_hi[j << kFenceShift] & kFenceMask over every list's
+    // entries (global entry index), fence_len = ceil(entries / 16); null:
+    // plain binary search
+    const uint64_t* fence;
+    uint64_t fence_len;
 };
+
+// One fence word per 16 entries: 128 bytes of high words, one L2 line.
+constexpr uint32_t kFenceShift = 4;
+// A fence word keeps the top 48 bits of its high word: the build's radix
+// passes leave those final (the run fix-up only reorders entries whose top 48
+// bits are equal), so the fix-up's first pass over the sorted words writes
+// the fence.  Comparing (kh &
+// kFenceMask) with a fence word still orders the key against the entry
+// whenever the two differ.
+constexpr uint64_t kFenceMask = ~0xFFFFull;
+// fence[j] = keys_hi[j << kFenceShift] & kFenceMask for j < ceil(total / 16).
+cudaError_t launch_fence(const uint64_t* keys_hi, uint64_t total, uint64_t* fence,
+                         cudaStream_t s);
 
 // p_query (device, nq entries, nullable) gives each query its own depth.
 // pos_in (device, nq x lists, nullable): lower_bound positions computed
@@ -107,17 +130,29 @@ struct IndexView {
 cudaError_t launch_entry_lo(const IndexView& ix, uint64_t* out, cudaStream_t s);
 // order (device, nq entries, nullable): warp w answers query order[w] (a
 // permutation of 0..nq-1); results still land at each query's own row.
+// pos_cm (device, nq x lists uint32, nullable): positions of
+// launch_batch_positions (curve-major rows), so the kernel skips its search.
 cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids, void* out_dist, cudaStream_t s,
                          const uint32_t* p_query = nullptr, const int64_t* pos_in = nullptr,
-                         const uint32_t* order = nullptr);
-// Bits of the curve-0 key that order a batch in hc_query_ordered: 65,536
-// buckets keep a batch's neighbouring queries together at two radix passes.
+                         const uint32_t* order = nullptr, const uint32_t* pos_cm = nullptr);
+// Bits of each curve's key that order a batch in hc_query_ordered: 65,536
+// buckets keep a batch's neighbouring queries together at two radix passes
+// (24 and 32 bits measured no faster on 1 to 32 partitions).
 constexpr uint32_t kOrderBits = 16;
-// The top kOrderBits bits of each query's curve-0 extended-key, as the low word of a
-// sort key (the order in which hc_query_ordered answers the queries).
-cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, uint64_t* keys,
-                              cudaStream_t s);
+// keys[c nq + i]: the top kOrderBits bits of query i's curve-c extended-key
+// for c < ncurves, as the low word of a sort key (curve 0: the order in which
+// hc_query_ordered answers the queries); qhi / qlo (nullable, same layout):
+// the keys' two words.
+cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, uint32_t ncurves,
+                              uint64_t* keys, uint64_t* qhi, uint64_t* qlo, cudaStream_t s);
+// lower_bound of every query in every list, one warp per 32 queries of one
+// curve's key order (order: curves x nq ranks -> query; qhi / qlo: curves x nq
+// query keys).  pos[i * lists + c * partitions + j] = position of query i in
+// list j * curves + c.
+cudaError_t launch_batch_positions(const IndexView& ix, uint32_t nq, const uint32_t* order,
+                                   const uint64_t* qhi, const uint64_t* qlo, uint32_t* pos,
+                                   cudaStream_t s);
 cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, int64_t* pos,
                              cudaStream_t s);
 cudaError_t launch_bruteforce(const void* db, hc_dtype dtype, uint64_t n, uint32_t d,

@@ -145,17 +145,19 @@ __device__ __forceinline__ uint64_t entry_key_lo(const IndexView& ix, uint32_t L
                       L % ix.P.curves);
 }
 
-// first i in [0, n) of list L (entries off ..) with key[i] >= (kh, kl), else n;
-// the low word is consulted only when the high words tie
-__device__ __forceinline__ uint32_t lower_bound_key(const IndexView& ix, uint32_t L, uint64_t off,
-                                                    uint32_t n, uint64_t kh, uint64_t kl) {
-    uint32_t first = 0, count = n;
+// first i in [first, first + count) (global entries of list L) with key[i] >=
+// (kh, kl), else first + count; the low word is consulted only when the high
+// words tie
+__device__ __forceinline__ uint64_t lower_bound_range(const IndexView& ix, uint32_t L,
+                                                      uint64_t first, uint32_t count,
+                                                      uint64_t end, uint64_t kh, uint64_t kl) {
     while (count > 0) {
-        const uint32_t step = count >> 1, mid = first + step;
-        if (!HC_IN_BOUNDS(kSiteSearch, mid, n)) break;
-        const uint64_t h = __ldg(ix.keys_hi + off + mid);
+        const uint32_t step = count >> 1;
+        const uint64_t mid = first + step;
+        if (!HC_IN_BOUNDS(kSiteSearch, mid, end)) break;
+        const uint64_t h = __ldg(ix.keys_hi + mid);
         bool less = h < kh;
-        if (h == kh) less = entry_key_lo(ix, L, off + mid) < kl;
+        if (h == kh) less = entry_key_lo(ix, L, mid) < kl;
         if (less) {
             first = mid + 1;
             count -= step + 1;
@@ -164,6 +166,193 @@ __device__ __forceinline__ uint32_t lower_bound_key(const IndexView& ix, uint32_
         }
     }
     return first;
+}
+
+// first i in [0, n) of list L (entries off ..) with key[i] >= (kh, kl), else n.
+// With a fence (the top 48 bits of every 16th high word of the index), the
+// fence words inside the list are searched first against pk = kh &
+// kFenceMask: the last one below pk and the first one above it bracket the
+// answer, which is then found among the at most 15 entries between them (one
+// 128-byte line of high words) instead of by probes spread over the whole
+// list.  Fence words equal to pk widen the bracket to the fence words that
+// tie.
+__device__ __forceinline__ uint32_t lower_bound_key(const IndexView& ix, uint32_t L, uint64_t off,
+                                                    uint32_t n, uint64_t kh, uint64_t kl) {
+    if (!ix.fence) return (uint32_t)(lower_bound_range(ix, L, off, n, off + n, kh, kl) - off);
+    const uint64_t ja = (off + 15) >> kFenceShift, jb = (off + n + 15) >> kFenceShift;
+    const uint64_t pk = kh & kFenceMask;
+    // jl = first fence point of the list whose fence word is >= pk
+    uint64_t jl = ja;
+    for (uint32_t count = (uint32_t)(jb - ja); count > 0;) {
+        const uint32_t step = count >> 1;
+        const uint64_t mid = jl + step;
+        if (!HC_IN_BOUNDS(kSiteSearch, mid, ix.fence_len)) break;
+        if (__ldg(ix.fence + mid) < pk) {
+            jl = mid + 1;
+            count -= step + 1;
+        } else {
+            count = step;
+        }
+    }
+    // entries before lo are below the key (fence point jl - 1 is); the entry
+    // at hi, a fence point whose word is above pk, is not
+    const uint64_t lo = jl > ja ? ((jl - 1) << kFenceShift) + 1 : off;
+    uint64_t hi = off + n;
+    if (jl < jb && HC_IN_BOUNDS(kSiteSearch, jl, ix.fence_len)) {
+        if (__ldg(ix.fence + jl) > pk) {
+            hi = jl << kFenceShift;
+        } else {
+            // fence points tying pk: the first one above it ends the bracket
+            uint64_t ju = jl + 1;
+            for (uint32_t count = (uint32_t)(jb - ju); count > 0;) {
+                const uint32_t step = count >> 1;
+                const uint64_t mid = ju + step;
+                if (!HC_IN_BOUNDS(kSiteSearch, mid, ix.fence_len)) break;
+                if (__ldg(ix.fence + mid) <= pk) {
+                    ju = mid + 1;
+                    count -= step + 1;
+                } else {
+                    count = step;
+                }
+            }
+            if (ju < jb) hi = ju << kFenceShift;
+        }
+    }
+    return (uint32_t)(lower_bound_range(ix, L, lo, (uint32_t)(hi - lo), off + n, kh, kl) - off);
+}
+
+// lower_bound_key of one key (kh, kl) in G lists at once (lists[g], skipped
+// where on[g] is false), the G searches in lockstep so that G loads are in
+// flight per lane.  Each search halves without branches (the probe picks the
+// half, the length shrinks by the same amount whatever the outcome), so lanes
+// searching lists of one length run the same steps: the fence points of the
+// list (first word >= kh & kFenceMask), the bracket, then the first entry of the bracket
+// whose key is >= (kh, kl).  pos[g] is list-relative.  Entry indexes fit 32
+// bits (an index holds fewer than 2^32 entries).
+template <int G>
+__device__ __forceinline__ void lower_bound_lists(const IndexView& ix, const uint32_t (&lists)[G],
+                                                  const bool (&on)[G], uint64_t kh, uint64_t kl,
+                                                  uint32_t (&pos)[G]) {
+    if (!ix.fence) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (!on[g]) continue;
+            const uint64_t off = ix.list_off[lists[g]];
+            pos[g] = lower_bound_key(ix, lists[g], off,
+                                     (uint32_t)(ix.list_off[lists[g] + 1] - off), kh, kl);
+        }
+        return;
+    }
+    const uint64_t pk = kh & kFenceMask;
+    uint32_t off[G], end[G], base[G], len[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        off[g] = on[g] ? (uint32_t)ix.list_off[lists[g]] : 0u;
+        end[g] = on[g] ? (uint32_t)ix.list_off[lists[g] + 1] : 0u;
+        base[g] = (uint32_t)(((uint64_t)off[g] + 15) >> kFenceShift);   // ja
+        len[g] = (uint32_t)(((uint64_t)end[g] + 15) >> kFenceShift) - base[g];
+    }
+    // fence points [ja, jb): the answer jl lies in [base, base + len]
+    for (;;) {
+        bool busy = false;
+        uint64_t f[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t mid = base[g] + (len[g] >> 1) - 1;
+            const bool go = len[g] > 1 && HC_IN_BOUNDS(kSiteSearch, mid, ix.fence_len);
+            f[g] = go ? __ldg(ix.fence + mid) : 0ull;
+            if (!go) len[g] = min(len[g], 1u);
+            busy |= go;
+        }
+        if (!busy) break;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (len[g] <= 1) continue;
+            const uint32_t half = len[g] >> 1;
+            base[g] += f[g] < pk ? half : 0u;
+            len[g] -= half;
+        }
+    }
+    // jl = base (+1 when the last candidate is below pk); fence word of jl
+    uint32_t jl[G];
+    uint64_t fj[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const bool one = len[g] == 1 && HC_IN_BOUNDS(kSiteSearch, base[g], ix.fence_len);
+        const uint64_t fb = one ? __ldg(ix.fence + base[g]) : 0ull;
+        jl[g] = base[g] + (one && fb < pk ? 1u : 0u);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const uint32_t jbg = (uint32_t)(((uint64_t)end[g] + 15) >> kFenceShift);
+        fj[g] = jl[g] < jbg && HC_IN_BOUNDS(kSiteSearch, jl[g], ix.fence_len)
+                    ? __ldg(ix.fence + jl[g]) : ~0ull;
+    }
+    // brackets [base, base + len) as in lower_bound_key
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const uint32_t ja = (uint32_t)(((uint64_t)off[g] + 15) >> kFenceShift);
+        const uint32_t jbg = (uint32_t)(((uint64_t)end[g] + 15) >> kFenceShift);
+        const uint32_t lo = jl[g] > ja ? ((jl[g] - 1) << kFenceShift) + 1 : off[g];
+        uint32_t hi = end[g];
+        if (jl[g] < jbg) {
+            if (fj[g] > pk) {
+                hi = jl[g] << kFenceShift;
+            } else {
+                // fence points tying pk: the first one above it ends the bracket
+                uint32_t ju = jl[g] + 1;
+                for (uint32_t cnt = jbg - ju; cnt > 0;) {
+                    const uint32_t step = cnt >> 1;
+                    const uint32_t mid = ju + step;
+                    if (!HC_IN_BOUNDS(kSiteSearch, mid, ix.fence_len)) break;
+                    if (__ldg(ix.fence + mid) <= pk) {
+                        ju = mid + 1;
+                        cnt -= step + 1;
+                    } else {
+                        cnt = step;
+                    }
+                }
+                if (ju < jbg) hi = ju << kFenceShift;
+            }
+        }
+        base[g] = lo;
+        len[g] = hi - lo;
+    }
+    // first entry of each bracket with key >= (kh, kl): the answer lies in
+    // [base, base + len]
+    for (;;) {
+        bool busy = false;
+        uint64_t h[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint32_t mid = base[g] + (len[g] >> 1) - 1;
+            const bool go = len[g] > 1 && HC_IN_BOUNDS(kSiteSearch, mid, end[g]);
+            h[g] = go ? __ldg(ix.keys_hi + mid) : 0ull;
+            if (!go) len[g] = min(len[g], 1u);
+            busy |= go;
+        }
+        if (!busy) break;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (len[g] <= 1) continue;
+            const uint32_t half = len[g] >> 1;
+            bool less = h[g] < kh;
+            if (h[g] == kh) less = entry_key_lo(ix, lists[g], base[g] + half - 1) < kl;
+            base[g] += less ? half : 0u;
+            len[g] -= half;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        uint32_t at = base[g];
+        if (len[g] == 1 && HC_IN_BOUNDS(kSiteSearch, at, end[g])) {
+            const uint64_t h = __ldg(ix.keys_hi + at);
+            bool less = h < kh;
+            if (h == kh) less = entry_key_lo(ix, lists[g], at) < kl;
+            at += less ? 1u : 0u;
+        }
+        if (on[g]) pos[g] = at - off[g];
+    }
 }
 
 // K1 + K3 for one query: positions of the query key in lists L0, L0 + Lstep,
@@ -190,6 +379,28 @@ __device__ __forceinline__ void query_positions(const IndexView& ix, const uint8
     __syncwarp();
 }
 
+// The query's positions in lists L0, L0 + Lstep, ... into pos_w[L]: read
+// from a batch pass when one ran (pos_in: list order, int64; pos_cm: curve-
+// major uint32, entry c * partitions + j for list j * curves + c), else
+// searched here.
+__device__ __forceinline__ void load_positions(const IndexView& ix, const uint8_t* qrow,
+                                               uint32_t* pos_w, int lane, uint32_t L0,
+                                               uint32_t Lstep, const int64_t* pos_in,
+                                               const uint32_t* pos_cm) {
+    if (pos_cm) {
+        const uint32_t curves = ix.P.curves, parts = ix.lists / curves;
+        for (uint32_t L = L0 + (uint32_t)lane * Lstep; L < ix.lists; L += 32 * Lstep)
+            pos_w[L] = __ldg(pos_cm + (L % curves) * parts + L / curves);
+        __syncwarp();
+    } else if (pos_in) {
+        for (uint32_t L = L0 + (uint32_t)lane * Lstep; L < ix.lists; L += 32 * Lstep)
+            pos_w[L] = (uint32_t)__ldg(pos_in + L);
+        __syncwarp();
+    } else {
+        query_positions(ix, qrow, pos_w, lane, L0, Lstep);
+    }
+}
+
 // Algorithm 2 for one query over the lists L0, L0 + Lstep, ... into the
 // warp's running top-k: keys, positions, then every window in 32-entry steps
 // (the next step's ids are loaded while the current rows are in flight).
@@ -197,14 +408,9 @@ template <bool F32, int LPR, int KR>
 __device__ __forceinline__ void search_lists(const IndexView& ix, const uint8_t* qrow,
                                              uint32_t depth, uint32_t k, uint32_t L0,
                                              uint32_t Lstep, uint32_t* pos_w, WarpTopK<KR>& top,
-                                             int lane, const int64_t* pos_in = nullptr) {
-    if (pos_in) {
-        for (uint32_t L = L0 + (uint32_t)lane * Lstep; L < ix.lists; L += 32 * Lstep)
-            pos_w[L] = (uint32_t)__ldg(pos_in + L);
-        __syncwarp();
-    } else {
-        query_positions(ix, qrow, pos_w, lane, L0, Lstep);
-    }
+                                             int lane, const int64_t* pos_in = nullptr,
+                                             const uint32_t* pos_cm = nullptr) {
+    load_positions(ix, qrow, pos_w, lane, L0, Lstep, pos_in, pos_cm);
     const uint32_t s = (uint32_t)lane % LPR;
     const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
     const uint8_t* db = static_cast<const uint8_t*>(ix.db);
@@ -362,15 +568,10 @@ __device__ __forceinline__ void search_lists_staged(const IndexView& ix, const u
                                                     uint32_t Lstep, uint32_t* pos_w,
                                                     uint32_t* win_pre, uint8_t* ring,
                                                     WarpTopK<KR>& top, int lane,
-                                                    const int64_t* pos_in = nullptr) {
+                                                    const int64_t* pos_in = nullptr,
+                                                    const uint32_t* pos_cm = nullptr) {
     static_assert(S >= 2, "one step reduced while another is in flight");
-    if (pos_in) {
-        for (uint32_t L = L0 + (uint32_t)lane * Lstep; L < ix.lists; L += 32 * Lstep)
-            pos_w[L] = (uint32_t)__ldg(pos_in + L);
-        __syncwarp();
-    } else {
-        query_positions(ix, qrow, pos_w, lane, L0, Lstep);
-    }
+    load_positions(ix, qrow, pos_w, lane, L0, Lstep, pos_in, pos_cm);
     const uint32_t s = (uint32_t)lane % LPR;
     const uint4 qv0 = s < (ix.row_bytes >> 4) ? ldg16(qrow + s * 16) : make_uint4(0, 0, 0, 0);
     const uint8_t* db = static_cast<const uint8_t*>(ix.db);

@@ -410,6 +410,7 @@ HC_API int hc_load(const char* path, const void* db_dev, void* cuda_stream, hc_i
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     int rc = index_alloc(x, s);
     if (!rc) rc = load_arrays(r, x, H, s);
+    if (!rc && x->fence) rc = status_of(launch_fence(x->keys_hi, H.total, x->fence, s));
     if (!rc) rc = verify_against_rows(x, s);
     if (rc) {
         cudaStreamSynchronize(s);

@@ -48,6 +48,7 @@ struct QueryArgs {
     const uint32_t* p_query;     // per-query depth (overrides p), or null
     const int64_t* pos_in;       // precomputed lower_bound positions (nq x lists), or null
     const uint32_t* order;       // warp w answers query order[w], or null (w itself)
+    const uint32_t* pos_cm;      // positions of the batch pass (curve-major rows), or null
 };
 
 #ifndef HC_QUERY_MIN_BLOCKS
@@ -78,26 +79,104 @@ __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kerne
                         (size_t)warp * kStages * 32 * ix.row_bytes;
         search_lists_staged<F32, LPR, KR, kStages>(
             ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, s_pre + warp * ix.lists, ring,
-            top, lane, a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
+            top, lane, a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr,
+            a.pos_cm ? a.pos_cm + (size_t)qi * ix.lists : nullptr);
     } else {
         search_lists<F32, LPR, KR>(ix, qrow, depth, a.k, 0, 1, s_pos + warp * ix.lists, top,
-                                   lane, a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr);
+                                   lane, a.pos_in ? a.pos_in + (size_t)qi * ix.lists : nullptr,
+                                   a.pos_cm ? a.pos_cm + (size_t)qi * ix.lists : nullptr);
     }
     top.template store<F32>(a.k, lane, a.out_ids + (size_t)qi * a.k,
                             static_cast<uint32_t*>(a.out_dist) + (size_t)qi * a.k);
 }
 
-// keys[i] = top kOrderBits bits of query i's curve-0 extended-key (one thread each)
+// keys[c nq + i] = top kOrderBits bits of query i's curve-c extended-key for
+// c < ncurves (one thread each); with qhi / qlo, also the key's two words
 __global__ void __launch_bounds__(256) order_keys_kernel(IndexView ix, const uint8_t* q,
-                                                         uint32_t nq, uint64_t* keys) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nq) return;
+                                                         uint32_t nq, uint32_t ncurves,
+                                                         uint64_t* keys, uint64_t* qhi,
+                                                         uint64_t* qlo) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)nq * ncurves) return;
+    const uint32_t c = (uint32_t)(t / nq), i = (uint32_t)(t % nq);
     uint64_t h, l;
-    curve_key_call(q + (size_t)i * ix.row_bytes, ix.P, 0, h, l);
+    curve_key_call(q + (size_t)i * ix.row_bytes, ix.P, c, h, l);
     const uint32_t bits = 8 * ix.P.m;   // key bits, right-aligned in (h, l)
     const uint64_t top = bits > 64 ? (h << (128 - bits)) | (bits < 128 ? l >> (bits - 64) : 0)
                                    : l << (64 - bits);
-    keys[i] = top >> (64 - kOrderBits);
+    keys[t] = top >> (64 - kOrderBits);
+    if (qhi) {
+        qhi[t] = h;
+        qlo[t] = l;
+    }
+}
+
+// partitions a lane of batch_positions_kernel searches side by side (1, 2
+// and 8 measured slower on 32 partitions; 4 keeps the kernel at 76 registers)
+constexpr int kBatchILP = 4;
+
+// at[0 .. G) to p[0 .. G), p aligned to 4 G bytes
+template <int G>
+__device__ __forceinline__ void store_group(uint32_t* p, const uint32_t (&at)[G]) {
+    if constexpr (G == 4) {
+        *reinterpret_cast<uint4*>(p) = make_uint4(at[0], at[1], at[2], at[3]);
+    } else if constexpr (G == 2) {
+        *reinterpret_cast<uint2*>(p) = make_uint2(at[0], at[1]);
+    } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) p[g] = at[g];
+    }
+}
+
+// K3 for a whole batch.  Warp w takes curve c = w / tiles and tile t = w %
+// tiles: the 32 queries at ranks 32 t .. 32 t + 31 of curve c's key order.
+// Each lane searches its query's curve-c key in list j * curves + c of every
+// partition j and writes the position to pos[query][c * partitions + j].  The
+// 32 keys of a warp are neighbours on curve c, so the lanes' probes fall on
+// the same few lines (one request serves many lanes) where lanes of a
+// per-query warp would each probe a different list.
+__global__ void __launch_bounds__(256) batch_positions_kernel(IndexView ix, uint32_t nq,
+                                                              const uint32_t* __restrict__ order,
+                                                              const uint64_t* __restrict__ qhi,
+                                                              const uint64_t* __restrict__ qlo,
+                                                              uint32_t* __restrict__ pos) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t curves = ix.P.curves, tiles = (nq + 31) / 32;
+    if (w >= (uint64_t)tiles * curves) return;
+    const uint32_t c = (uint32_t)(w / tiles), t = (uint32_t)(w % tiles);
+    const uint32_t r = t * 32 + (uint32_t)lane;
+    bool live = r < nq;
+    uint32_t qi = live ? __ldg(order + (size_t)c * nq + r) : 0u;
+    if (live && !HC_IN_BOUNDS(kSiteQuery, qi, nq)) {
+        live = false;
+        qi = 0;
+    }
+    // lanes past the batch search with query 0's key and write nothing
+    const uint64_t kh = __ldg(qhi + (size_t)c * nq + qi), kl = __ldg(qlo + (size_t)c * nq + qi);
+    const uint32_t parts = ix.lists / curves;
+    uint32_t* out = pos + (size_t)qi * ix.lists + (size_t)c * parts;
+    // kBatchILP partitions at a time: their searches share the key
+    for (uint32_t j0 = 0; j0 < parts; j0 += kBatchILP) {
+        uint32_t lists[kBatchILP], at[kBatchILP];
+        bool on[kBatchILP];
+#pragma unroll
+        for (int g = 0; g < kBatchILP; ++g) {
+            on[g] = j0 + g < parts;
+            lists[g] = on[g] ? (j0 + g) * curves + c : 0u;
+        }
+        lower_bound_lists<kBatchILP>(ix, lists, on, kh, kl, at);
+        if (!live) continue;
+        if (parts % kBatchILP == 0) {
+            // whole groups: one vector store (the row offset is a multiple
+            // of the group since partitions are)
+            store_group(out + j0, at);
+        } else {
+#pragma unroll
+            for (int g = 0; g < kBatchILP; ++g)
+                if (on[g]) out[j0 + g] = at[g];
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kQWarps * 32) positions_kernel(QueryArgs a) {
@@ -110,6 +189,14 @@ __global__ void __launch_bounds__(kQWarps * 32) positions_kernel(QueryArgs a) {
     query_positions(a.ix, qrow, pos_w, lane);
     for (uint32_t L = lane; L < a.ix.lists; L += 32)
         a.out_pos[(size_t)qi * a.ix.lists + L] = (int64_t)pos_w[L];
+}
+
+// fence[j] = keys_hi[16 j] & kFenceMask: one thread per fence word
+__global__ void __launch_bounds__(256) fence_kernel(const uint64_t* __restrict__ keys_hi,
+                                                    uint64_t len, uint64_t* __restrict__ fence) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < len; j += stride)
+        fence[j] = __ldg(keys_hi + (j << kFenceShift)) & kFenceMask;
 }
 
 template <bool F32, int LPR, int KR>
@@ -144,18 +231,43 @@ struct QueryLaunch {
 cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32_t k, uint32_t p,
                          int32_t* out_ids, void* out_dist, cudaStream_t s,
                          const uint32_t* p_query, const int64_t* pos_in,
-                         const uint32_t* order) {
+                         const uint32_t* order, const uint32_t* pos_cm) {
     if (nq == 0) return cudaSuccess;
-    QueryArgs a{ix, q, nq, k, p, out_ids, out_dist, nullptr, p_query, pos_in, order};
+    QueryArgs a{ix, q, nq, k, p, out_ids, out_dist, nullptr, p_query, pos_in, order, pos_cm};
     return dispatch<QueryLaunch>(ix.P.dtype == HC_F32, lanes_per_row(ix.row_bytes), regs_for_k(k),
                                  a, s);
 }
 
-cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, uint64_t* keys,
-                              cudaStream_t s) {
-    if (nq == 0) return cudaSuccess;
-    order_keys_kernel<<<(nq + 255) / 256, 256, 0, s>>>(ix, static_cast<const uint8_t*>(q), nq,
-                                                       keys);
+cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, uint32_t ncurves,
+                              uint64_t* keys, uint64_t* qhi, uint64_t* qlo, cudaStream_t s) {
+    const uint64_t total = (uint64_t)nq * ncurves;
+    if (total == 0) return cudaSuccess;
+    order_keys_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        ix, static_cast<const uint8_t*>(q), nq, ncurves, keys, qhi, qlo);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_positions(const IndexView& ix, uint32_t nq, const uint32_t* order,
+                                   const uint64_t* qhi, const uint64_t* qlo, uint32_t* pos,
+                                   cudaStream_t s) {
+    const uint64_t warps = (uint64_t)((nq + 31) / 32) * ix.P.curves;
+    if (warps == 0) return cudaSuccess;
+    batch_positions_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(ix, nq, order, qhi, qlo,
+                                                                       pos);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fence(const uint64_t* keys_hi, uint64_t total, uint64_t* fence,
+                         cudaStream_t s) {
+    const uint64_t len = (total + 15) >> kFenceShift;
+    if (len == 0) return cudaSuccess;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (len + 255) / 256, cap = (uint64_t)std::max(sms, 1) * 8;
+    fence_kernel<<<(unsigned)std::min(want, cap), 256, 0, s>>>(keys_hi, len, fence);
     count_launches(1);
     return cudaGetLastError();
 }

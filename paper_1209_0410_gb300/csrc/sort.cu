@@ -445,12 +445,16 @@ constexpr int kLaneRun = 8;   // runs ordered inside find_runs: at most this lon
 // chunk's edge, or with equal high words, which need the low words) has its
 // start listed for sort_runs.  A run's records are permuted among the run's
 // own positions, so the prefix at every position -- all that neighbouring
-// chunks read here -- never changes.  run_shift <= 32.
+// chunks read here -- never changes.  run_shift <= 32.  For the same reason
+// the fence (nullable; only when kFenceMask clears the run_shift low bits) is
+// final here: fence[i / 16] = hi[i] & kFenceMask for every position i that is
+// a multiple of 16.
 template <int SHIFT>
 __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
     uint64_t* __restrict__ hi, uint32_t* __restrict__ ids, uint32_t nseg,
     const SegInfo* __restrict__ segs, uint64_t* __restrict__ run_pos,
-    uint32_t* __restrict__ run_seg, unsigned long long* __restrict__ nruns) {
+    uint32_t* __restrict__ run_seg, unsigned long long* __restrict__ nruns,
+    uint64_t* __restrict__ fence) {
     static_assert(kFindChunks % kFindBatch == 0, "whole batches");
     static_assert(SHIFT > 0 && SHIFT <= 32, "low bits in a 32-bit word");
     __shared__ uint32_t masks[kFindWarps][kFindChunks];
@@ -466,6 +470,12 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
     // the segment goes on before this tile / after its last record
     const bool tile_after = lt + 1 < si.ntiles;
     uint32_t found = 0;
+    // fence words of the warp's 32 x 16 records: word l (lane l) is the high
+    // word at wpos0 + 16 l, the l-th position of the warp that is a multiple of
+    // 16; chunk c holds words 2c and 2c + 1 at its offsets a0 and a0 + 16
+    const uint64_t wbeg = start + (uint64_t)warp * kFindChunks * 32;
+    const uint32_t a0 = (uint32_t)((16 - (wbeg & 15)) & 15);
+    uint64_t fw = 0;
     for (int c0 = 0; c0 < kFindChunks; c0 += kFindBatch) {
         // a chunk's words and ids, plus the word before it (lane 0) or after
         // it (lane 31)
@@ -482,6 +492,16 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
             if (ok && lane == 0 && (lt > 0 || off > 0)) h = hi[i - 1];
             if (ok && lane == 31 && (off + 1 < count || tile_after)) h = hi[i + 1];
             halo[j] = h;
+        }
+        if (fence) {
+#pragma unroll
+            for (int j = 0; j < kFindBatch; ++j) {
+                const uint32_t c = (uint32_t)(c0 + j);
+                const uint64_t f0 = __shfl_sync(0xffffffffu, hv[j], (int)a0);
+                const uint64_t f1 = __shfl_sync(0xffffffffu, hv[j], (int)a0 + 16);
+                if ((uint32_t)lane == 2 * c) fw = f0;
+                if ((uint32_t)lane == 2 * c + 1) fw = f1;
+            }
         }
 #pragma unroll
         for (int j = 0; j < kFindBatch; ++j) {
@@ -543,6 +563,11 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
             if (lane == 0) masks[warp][c0 + j] = listed;
             found += (uint32_t)__popc(listed);
         }
+    }
+    if (fence) {
+        // one coalesced store of the warp's fence words
+        const uint64_t fpos = wbeg + a0 + 16 * (uint64_t)lane;
+        if (fpos < start + count) fence[fpos >> kFenceShift] = fw & kFenceMask;
     }
     if (lane == 0) wbase[warp] = found;
     __syncthreads();
@@ -1056,7 +1081,10 @@ cudaError_t upload_small(void* dst, const void* src, size_t bytes, cudaStream_t 
     return cudaSuccess;
 }
 
-int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
+namespace {
+
+// The sort; fenced: the fence was written on the way (find_runs).
+int sort_body(const SortProblem& p, void* scratch, cudaStream_t s, bool& fenced) {
     if (p.seg_off.size() < 2 || p.key_bits < 1 || p.key_bits > 128) return HC_ERR_ARG;
     Layout L = make_layout(p);
     if (L.total == 0) return HC_OK;
@@ -1132,11 +1160,16 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
             uint64_t* run_pos = reinterpret_cast<uint64_t*>(pa);
             uint32_t* run_seg = pb;
             uint4* long_list = reinterpret_cast<uint4*>(base + L.off_long);
+            // the fence from find_runs when its mask clears every bit the
+            // fix-up may still change (the low 8 skip bits)
+            uint64_t* fence =
+                (kFenceMask & ((1ull << (8 * skip)) - 1)) == 0 ? p.out_fence : nullptr;
+            fenced = fence != nullptr;
             switch (skip) {
 #define HC_FIND(K)                                                                          \
     case K:                                                                                 \
         find_runs_kernel<8 * K><<<L.ntiles, kFindWarps * 32, 0, s>>>(                       \
-            p.out_hi, p.out_ids, L.nseg, segs, run_pos, run_seg, nruns);                    \
+            p.out_hi, p.out_ids, L.nseg, segs, run_pos, run_seg, nruns, fence);             \
         break;
                 HC_FIND(1) HC_FIND(2) HC_FIND(3) HC_FIND(4)
 #undef HC_FIND
@@ -1234,6 +1267,17 @@ int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
     count_launches(1);
     if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
     return HC_OK;
+}
+
+}  // namespace
+
+int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s) {
+    bool fenced = false;
+    int rc = sort_body(p, scratch, s, fenced);
+    if (rc == HC_OK && p.out_fence && !fenced &&
+        launch_fence(p.out_hi, p.seg_off.back(), p.out_fence, s) != cudaSuccess)
+        rc = HC_ERR_CUDA;
+    return rc;
 }
 
 }  // namespace hc

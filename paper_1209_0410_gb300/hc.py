@@ -115,7 +115,7 @@ def load_library(path):
     L.hc_query_depths.argtypes = [_vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp]
     L.hc_query_at.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp, _vp]
     L.hc_query_ordered_workspace.restype = ctypes.c_size_t
-    L.hc_query_ordered_workspace.argtypes = [_u32]
+    L.hc_query_ordered_workspace.argtypes = [_vp, _u32]
     L.hc_query_ordered.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp,
                                    ctypes.c_size_t, _vp]
     L.hc_serve_create_ex.argtypes = [ctypes.POINTER(_vp), _u32, _u64,
@@ -349,22 +349,23 @@ def hc_query_at(index, q, k, p, positions, out_ids=None, out_dist=None, stream=N
     return out_ids, out_dist
 
 
-def hc_query_ordered_workspace(nq):
-    """Bytes of device workspace hc_query_ordered needs for nq queries."""
-    return int(lib().hc_query_ordered_workspace(nq))
+def hc_query_ordered_workspace(index, nq):
+    """Bytes of device workspace hc_query_ordered needs for nq queries on
+    this index (on any index of the same curves and lists)."""
+    return int(lib().hc_query_ordered_workspace(index.handle, nq))
 
 
 def hc_query_ordered(index, q, k, p, out_ids=None, out_dist=None, workspace=None, stream=None):
     """hc_query answering the queries in curve-0 key order (results identical);
-    workspace: a CUDA uint8 tensor of at least hc_query_ordered_workspace(nq)
-    bytes (allocated here when None)."""
+    workspace: a CUDA uint8 tensor of at least
+    hc_query_ordered_workspace(index, nq) bytes (allocated here when None)."""
     nq = q.shape[0]
     if out_ids is None:
         out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
     if out_dist is None:
         out_dist = torch.empty((nq, k), dtype=_dist_dtype(index.dtype), device=q.device)
     if nq:
-        need = hc_query_ordered_workspace(nq)
+        need = hc_query_ordered_workspace(index, nq)
         if workspace is None:
             workspace = torch.empty(need, dtype=torch.uint8, device=q.device)
         _check(lib().hc_query_ordered(index.handle, _dev(q, "q"), nq, k, p,

@@ -388,11 +388,68 @@ def test_query_ordered_other_key_widths(hc, d, curves, m):
     idx.free()
 
 
+@pytest.mark.parametrize("parts,curves,m,nq", [(8, 8, 16, 1000), (32, 8, 16, 333),
+                                                (16, 16, 8, 65), (256, 1, 16, 40),
+                                                (3, 32, 4, 97)])
+def test_query_ordered_batch_search_many_lists(hc, parts, curves, m, nq):
+    """The ordered path's batch search (a warp per 32 neighbouring keys of one
+    curve, over that curve's list in every partition) gives the positions of
+    Algorithm 2: the walk over up to 256 lists equals the oracle's search,
+    with batches that end in a partial warp."""
+    db, q = make_case(20011, nq, seed=parts * 7 + curves)
+    idx = hc.hc_build(dev(db), curves=curves, dims_per_curve=m, partitions=parts)
+    ids, dist = hc.hc_query_ordered(idx, dev(q), 10, 6)
+    sync()
+    oidx = O.build(db, curves=curves, m=m, ell=parts)
+    rids, rdist = O.search(oidx, db, q, 10, 6)
+    assert np.array_equal(ids.cpu().numpy(), rids)
+    assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+    idx.free()
+
+
+def nibble_variants(rng, row, count):
+    """Rows equal to `row` in the top 4 bits of every coordinate: their keys
+    share the high word (the top 4 bits of each of a curve's 16 coordinates)
+    and differ in the low word."""
+    low = rng.integers(0, 16, size=(count, row.shape[0]), dtype=np.uint8)
+    return (row & np.uint8(0xF0))[None, :] | low
+
+
+@pytest.mark.parametrize("parts", [1, 3])
+def test_searches_with_high_words_tied_across_fence_blocks(hc, parts):
+    """Entries whose high words tie over runs of 16 to 700 entries (many
+    16-entry fence blocks, fence words equal to the query's high word) and
+    queries that tie them: the lower_bound falls back to the low words, and
+    the positions of both search paths (per-query warps, the ordered batch
+    pass) and the answers equal the oracle's."""
+    rng = np.random.default_rng(29)
+    base = rng.integers(0, 256, size=(3, 128), dtype=np.uint8)
+    db = np.concatenate([rng.integers(0, 256, size=(3000, 128), dtype=np.uint8),
+                         nibble_variants(rng, base[0], 700), nibble_variants(rng, base[1], 40),
+                         nibble_variants(rng, base[2], 16)])
+    db = db[rng.permutation(len(db))]
+    q = np.concatenate([nibble_variants(rng, base[0], 30), nibble_variants(rng, base[1], 10),
+                        nibble_variants(rng, base[2], 5), db[:25]])
+    idx = hc.hc_build(dev(db), partitions=parts)
+    oidx = O.build(db, curves=8, m=16, ell=parts)
+    rids, rdist, opos = O.search(oidx, db, q, 10, 24, return_pos=True)
+    pos = hc.hc_query_positions(idx, dev(q))
+    ids_a, dist_a = hc.hc_query(idx, dev(q), 10, 24)
+    ids_b, dist_b = hc.hc_query_ordered(idx, dev(q), 10, 24)
+    sync()
+    assert np.array_equal(pos.cpu().numpy(), opos)
+    for ids, dist in ((ids_a, dist_a), (ids_b, dist_b)):
+        assert np.array_equal(ids.cpu().numpy(), rids)
+        assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+    idx.free()
+
+
 def test_query_ordered_rejects_a_small_workspace(hc):
     import torch
     db, q = make_case(5000, 100, seed=2)
     idx = hc.hc_build(dev(db))
-    ws = torch.empty(hc.hc_query_ordered_workspace(100) - 256, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(hc.hc_query_ordered_workspace(idx, 100) - 256, dtype=torch.uint8,
+                     device="cuda")
     with pytest.raises(hc.HCError):
         hc.hc_query_ordered(idx, dev(q), 10, 20, workspace=ws)
     idx.free()

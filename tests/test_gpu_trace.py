@@ -1,6 +1,7 @@
 """NVTX ranges of the device paths, recorded by the injection library in a
 child process: hc_build opens "hc_build" with its "keys" and "sort" phases,
-hc_query_ordered its "order" and "walk" phases, and every range closes."""
+hc_query_ordered its "order", "search" and "walk" phases, and every range
+closes."""
 import pytest
 
 from trace_tools import balanced, record
@@ -35,7 +36,7 @@ def test_device_paths_record_their_ranges(tmp_path):
 
     text = "\n".join(lines)
     build = ["push hc hc_build"] + seq("keys", "sort") + ["pop hc"]
-    ordered = ["push hc hc_query_ordered"] + seq("order", "walk") + ["pop hc"]
+    ordered = ["push hc hc_query_ordered"] + seq("order", "search", "walk") + ["pop hc"]
     assert "\n".join(build) in text
     assert "\n".join(["push hc hc_query", "pop hc"]) in text
     assert "\n".join(ordered) in text

@@ -84,7 +84,7 @@ def test_build_bytes_counts_every_pass():
     p1 = 8 * r + counts + 8 * r + 13 * r
     p2 = 1 * r + counts + 12 * r + 13 * r
     p3 = 1 * r + counts + 12 * r + 12 * r
-    assert ker == pytest.approx(keys + p1 + p2 + p3 + 12 * r)
+    assert ker == pytest.approx(keys + p1 + p2 + p3 + 12 * r + 0.5 * r)
     # the headline workload (6 passes): about 16.0 GB moved per build
     _, k10 = bench.build_bytes(10_000_000, 128, 8)
     assert 15.5e9 < k10 < 16.5e9
