@@ -453,12 +453,29 @@ def run_partitions(a):
                 hc.hc_query(idx, tq, k, phi, ids, dist)
             e1.record(stream)
             torch.cuda.synchronize()
+            plain_ms = e0.elapsed_time(e1) / reps
+            # the ordered path: every curve's key order, one batch lower_bound
+            # pass, then the walk (the same results)
+            ws = torch.empty(hc.hc_query_ordered_workspace(idx, nq), dtype=torch.uint8,
+                             device="cuda")
+            o_ids = torch.empty_like(ids)
+            o_dist = torch.empty_like(dist)
+            hc.hc_query_ordered(idx, tq, k, phi, o_ids, o_dist, workspace=ws)
+            e0, e1 = _events()
+            e0.record(stream)
+            for _ in range(reps):
+                hc.hc_query_ordered(idx, tq, k, phi, o_ids, o_dist, workspace=ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
+            same = bool(torch.equal(ids, o_ids) and torch.equal(dist, o_dist))
+            del ws
             if seq_ids is None:
                 seq_ids, seq_dist = ids.clone(), dist.clone()
             row = {"ell": ell, "setting": name, "slack": float(slack), "phi": phi,
                    "bound_eq6": partition.equiv_bound(Phi, ell, phi) if ell > 1 else 0.0,
                    "build_ms": build_ms, "query_ms": ms, "qps": nq / (ms / 1e3),
+                   "plain_query_ms": plain_ms, "ordered_equals_plain": same,
                    "window_rows_per_query": 2 * phi * ell * 8,
                    "recall_at_10": learned.recall_at_10(ids[:rs], dist[:rs], tdist),
                    "equal_to_sequential": learned.agreement(ids, seq_ids),
@@ -476,5 +493,8 @@ def run_partitions(a):
                                   "Phi=%d per side, k=%d, ell in {1..32} contiguous "
                                   "partitions, Optimist / Pessimist slack" % (n, nq, Phi, k),
                       "l2": "inputs larger than L2 (database %.2f GB)" % (n * 128 / 1e9),
+                      "query_path": "hc_query_ordered (per-curve key orders, one batch "
+                                    "lower_bound pass, walk in curve-0 order; results equal "
+                                    "hc_query, whose time is plain_query_ms)",
                       "recall_sample_queries": rs, "sweep": rows}})
     return 0
