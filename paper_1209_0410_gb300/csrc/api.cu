@@ -550,6 +550,7 @@ int enqueue_ordered(hc_index* idx, const void* q_dev, uint32_t nq, uint32_t k, u
     sp.out_hi = reinterpret_cast<uint64_t*>(ws + L.out_hi);
     sp.out_lo = reinterpret_cast<uint64_t*>(ws + L.out_lo);
     sp.out_ids = reinterpret_cast<uint32_t*>(ws + L.order);
+    sp.ids_only = true;   // the permutations alone
     {
         TraceRange to("order");
         if ((rc = sort_segments(sp, ws + L.sort, s))) return rc;

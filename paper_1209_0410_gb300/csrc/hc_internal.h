@@ -79,6 +79,10 @@ struct SortProblem {
     // first path (the bits of the high word the radix passes leave final),
     // else by a pass over out_hi after the sort
     uint64_t* out_fence = nullptr;
+    // only out_ids is wanted (affine ids: id_base_dev set, keys of at most 64
+    // bits): the last radix pass writes the ids and nothing is gathered;
+    // out_hi and out_lo serve as scratch and are left undefined
+    bool ids_only = false;
 };
 // Scratch bytes the sort needs for this problem (queried before allocating).
 size_t sort_scratch_bytes(const SortProblem& p);

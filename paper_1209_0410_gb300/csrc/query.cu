@@ -90,17 +90,14 @@ __global__ void __launch_bounds__(kQWarps * 32, HC_QUERY_MIN_BLOCKS) query_kerne
                             static_cast<uint32_t*>(a.out_dist) + (size_t)qi * a.k);
 }
 
-// keys[c nq + i] = top kOrderBits bits of query i's curve-c extended-key for
-// c < ncurves (one thread each); with qhi / qlo, also the key's two words
-__global__ void __launch_bounds__(256) order_keys_kernel(IndexView ix, const uint8_t* q,
-                                                         uint32_t nq, uint32_t ncurves,
-                                                         uint64_t* keys, uint64_t* qhi,
-                                                         uint64_t* qlo) {
-    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (uint64_t)nq * ncurves) return;
-    const uint32_t c = (uint32_t)(t / nq), i = (uint32_t)(t % nq);
-    uint64_t h, l;
-    curve_key_call(q + (size_t)i * ix.row_bytes, ix.P, c, h, l);
+// keys[c nq + i] = top kOrderBits bits of query i's curve-c extended-key
+// for c < ncurves; with qhi / qlo, also the key's two words.  One thread per
+// query: 16-coordinate curves of consecutive dimensions four at a time as
+// byte lanes of 32-bit words (as the build's key pass), others one by one.
+__device__ __forceinline__ void put_order_key(const IndexView& ix, uint32_t nq, uint32_t i,
+                                              uint32_t c, uint64_t h, uint64_t l, uint64_t* keys,
+                                              uint64_t* qhi, uint64_t* qlo) {
+    const size_t t = (size_t)c * nq + i;
     const uint32_t bits = 8 * ix.P.m;   // key bits, right-aligned in (h, l)
     const uint64_t top = bits > 64 ? (h << (128 - bits)) | (bits < 128 ? l >> (bits - 64) : 0)
                                    : l << (64 - bits);
@@ -108,6 +105,32 @@ __global__ void __launch_bounds__(256) order_keys_kernel(IndexView ix, const uin
     if (qhi) {
         qhi[t] = h;
         qlo[t] = l;
+    }
+}
+
+__global__ void __launch_bounds__(256) order_keys_kernel(IndexView ix, const uint8_t* q,
+                                                         uint32_t nq, uint32_t ncurves,
+                                                         uint64_t* keys, uint64_t* qhi,
+                                                         uint64_t* qlo) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    const uint8_t* row = q + (size_t)i * ix.row_bytes;
+    uint32_t c = 0;
+    if (ix.P.m == 16 && ix.P.dim_map == nullptr) {
+        for (; c + 4 <= ncurves; c += 4) {
+            uint4 cb[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) cb[t] = curve_bytes16(row, ix.P.dtype, c + t);
+            uint64_t hi[4], lo[4];
+            hilbert_keys4<false>(cb, hi, lo);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) put_order_key(ix, nq, i, c + t, hi[t], lo[t], keys, qhi, qlo);
+        }
+    }
+    for (; c < ncurves; ++c) {
+        uint64_t h, l;
+        curve_key_call(row, ix.P, c, h, l);
+        put_order_key(ix, nq, i, c, h, l, keys, qhi, qlo);
     }
 }
 
@@ -240,10 +263,9 @@ cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32
 
 cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, uint32_t ncurves,
                               uint64_t* keys, uint64_t* qhi, uint64_t* qlo, cudaStream_t s) {
-    const uint64_t total = (uint64_t)nq * ncurves;
-    if (total == 0) return cudaSuccess;
-    order_keys_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        ix, static_cast<const uint8_t*>(q), nq, ncurves, keys, qhi, qlo);
+    if (nq == 0 || ncurves == 0) return cudaSuccess;
+    order_keys_kernel<<<(nq + 255) / 256, 256, 0, s>>>(ix, static_cast<const uint8_t*>(q), nq,
+                                                       ncurves, keys, qhi, qlo);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1227,17 +1227,18 @@ int sort_body(const SortProblem& p, void* scratch, cudaStream_t s, bool& fenced)
     // digits of the next pass were written by the previous scatter when both
     // passes read the same key word
     bool have_digits = false;
-    auto run_pass = [&](int digit, bool next_same_word) -> int {
+    // final_ids: the pass writes the final ids (id_base) instead of positions
+    auto run_pass = [&](int digit, bool next_same_word, bool final_ids = false) -> int {
         const int shift = (digit & 7) * 8;
         if (L.ntiles) {
             hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cur_w, have_digits ? dgt : nullptr, shift,
                                                       L.nseg, segs, counts);
             scan_kernel<<<scan_grid, kScanThreads, 0, s>>>(segs, counts, totals);
             uint64_t* wd = wbuf[wnext];
-            uint32_t* pd = pbuf[pnext];
+            uint32_t* pd = final_ids ? p.out_ids : pbuf[pnext];
             scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(
-                cur_w, cur_p, wd, pd, shift, L.nseg, segs, counts, totals, nullptr,
-                next_same_word ? dgt : nullptr);
+                cur_w, cur_p, wd, pd, shift, L.nseg, segs, counts, totals,
+                final_ids ? p.id_base_dev : nullptr, next_same_word ? dgt : nullptr);
             count_launches(3);
             if (cudaGetLastError() != cudaSuccess) return HC_ERR_CUDA;
             cur_w = wd;
@@ -1248,6 +1249,13 @@ int sort_body(const SortProblem& p, void* scratch, cudaStream_t s, bool& fenced)
         have_digits = next_same_word;
         return HC_OK;
     };
+    if (p.ids_only && hi_passes == 0 && p.id_base_dev) {
+        // the last pass writes the ids; no word is gathered
+        for (int t = 0; t < lo_passes; ++t)
+            if (int rc = run_pass(t, t + 1 < lo_passes && (t & 7) != 7, t + 1 == lo_passes))
+                return rc;
+        return HC_OK;
+    }
     for (int t = 0; t < lo_passes; ++t)
         if (int rc = run_pass(t, t + 1 < lo_passes && (t & 7) != 7)) return rc;
     {
