@@ -6,8 +6,9 @@ The oracle builds its own index over all 10M rows (Algorithm 1, ~10 s on the
 host cores); every one of the 80M list entries must match the GPU's, and a
 seeded sample of the queries is searched by the oracle one by one and must
 match the GPU's full-batch results bit for bit (ids and int32 distances), at
-p = 32, 128 and 512.  The float32 variant (x = u/255) is checked the same way
-on a sample, within 1e-5 relative.
+p = 32, 128 and 512, through hc_query and through hc_query_ordered (the
+bench's launch sequence), and with 8 and 32 partitions.  The float32 variant
+(x = u/255) is checked the same way on a sample, within 1e-5 relative.
 """
 import numpy as np
 import pytest
@@ -74,6 +75,36 @@ def test_full_batch_query_sampled_bit_exact(hc, data, gpu_index, oracle_index, p
     ids, dist = hc.hc_query(gpu_index, torch.from_numpy(q).cuda(), K, p)
     torch.cuda.synchronize()
     rids, rdist = O.search(oracle_index, db, q[pick], K, p)
+    assert np.array_equal(ids.cpu().numpy()[pick], rids)
+    assert np.array_equal(dist.cpu().numpy()[pick], O.int32_dist(rdist))
+
+
+def test_full_batch_ordered_query_sampled_bit_exact(hc, data, gpu_index, oracle_index):
+    """The launch sequence bench.py times: hc_query_ordered (order keys of
+    every curve, the batch lower_bound pass over the fence, the walk in
+    curve-0 key order) over the whole batch at p = 128."""
+    import torch
+    db, q, pick = data
+    ids, dist = hc.hc_query_ordered(gpu_index, torch.from_numpy(q).cuda(), K, 128)
+    torch.cuda.synchronize()
+    rids, rdist = O.search(oracle_index, db, q[pick], K, 128)
+    assert np.array_equal(ids.cpu().numpy()[pick], rids)
+    assert np.array_equal(dist.cpu().numpy()[pick], O.int32_dist(rdist))
+
+
+@pytest.mark.parametrize("ell,phi", [(32, 4), (8, 32)])
+def test_full_size_partitioned_ordered_sampled(hc, data, ell, phi):
+    """Partitioned Hypercurves at full size (256 and 64 lists of 0.3M and
+    1.25M entries): the ordered path's batch search and walk against the
+    oracle's partitioned Algorithm 2 on the sampled queries."""
+    import torch
+    db, q, pick = data
+    idx = hc.hc_build(torch.from_numpy(db).cuda(), 8, 16, partitions=ell)
+    ids, dist = hc.hc_query_ordered(idx, torch.from_numpy(q).cuda(), K, phi)
+    torch.cuda.synchronize()
+    idx.free()
+    oidx = O.build(db, curves=8, m=16, ell=ell)
+    rids, rdist = O.search(oidx, db, q[pick], K, phi)
     assert np.array_equal(ids.cpu().numpy()[pick], rids)
     assert np.array_equal(dist.cpu().numpy()[pick], O.int32_dist(rdist))
 
