@@ -575,10 +575,12 @@ int enqueue_host_query(hc_index* idx, const void* q_host, uint32_t nq, uint32_t 
     const size_t qbytes = (size_t)nq * idx->row_bytes;
     const size_t obytes = (size_t)nq * k * 4;
     // large batches are answered in curve-0 key order (hc_query_ordered: the
-    // same results, fewer DRAM reads); its workspace follows the queries
+    // same results, fewer DRAM reads); its workspace follows the results, on
+    // the walk's stream, so that only the query buffer comes and goes in the
+    // copy stream's order
     const bool ordered = nq >= kHostOrderedMin;
-    const size_t ws_off = align256(qbytes);
-    const size_t st_bytes = ordered ? ws_off + order_layout(idx, nq).bytes : qbytes;
+    const size_t ws_off = align256(2 * obytes);
+    const size_t out_bytes = ordered ? ws_off + order_layout(idx, nq).bytes : 2 * obytes;
     int rc;
     if (!idx->st_done &&
         (rc = status_of(cudaEventCreateWithFlags(&idx->st_done, cudaEventDisableTiming))))
@@ -588,19 +590,19 @@ int enqueue_host_query(hc_index* idx, const void* q_host, uint32_t nq, uint32_t 
     // the query buffer is allocated in the copy stream's order
     keep_pool_memory();
     if ((rc = status_of(cudaStreamWaitEvent(cs, idx->st_done, 0)))) return rc;
-    if (st_bytes > idx->st_q_cap) {
+    if (qbytes > idx->st_q_cap) {
         pool_free(idx->st_q, cs);
         idx->st_q = nullptr;
         idx->st_q_cap = 0;
-        if ((rc = dev_alloc_async(&idx->st_q, st_bytes, cs))) return rc;
-        idx->st_q_cap = st_bytes;
+        if ((rc = dev_alloc_async(&idx->st_q, qbytes, cs))) return rc;
+        idx->st_q_cap = qbytes;
     }
-    if (2 * obytes > idx->st_out_cap) {
+    if (out_bytes > idx->st_out_cap) {
         pool_free(idx->st_out, s);
         idx->st_out = nullptr;
         idx->st_out_cap = 0;
-        if ((rc = dev_alloc_async(&idx->st_out, 2 * obytes, s))) return rc;
-        idx->st_out_cap = 2 * obytes;
+        if ((rc = dev_alloc_async(&idx->st_out, out_bytes, s))) return rc;
+        idx->st_out_cap = out_bytes;
     }
     int32_t* d_ids = static_cast<int32_t*>(idx->st_out);
     void* d_dist = static_cast<char*>(idx->st_out) + obytes;
@@ -615,7 +617,7 @@ int enqueue_host_query(hc_index* idx, const void* q_host, uint32_t nq, uint32_t 
         if (rc) return rc;
     }
     rc = ordered ? enqueue_ordered(idx, idx->st_q, nq, k, p, d_ids, d_dist,
-                                   static_cast<char*>(idx->st_q) + ws_off, s)
+                                   static_cast<char*>(idx->st_out) + ws_off, s)
                  : status_of(launch_query(view_of(idx), idx->st_q, nq, k, p, d_ids, d_dist, s));
     if (rc) return rc;
     if ((rc = status_of(cudaMemcpyAsync(out_ids_host, d_ids, obytes, cudaMemcpyDeviceToHost, s))))
