@@ -221,29 +221,31 @@ __device__ __forceinline__ uint32_t lower_bound_key(const IndexView& ix, uint32_
     return (uint32_t)(lower_bound_range(ix, L, lo, (uint32_t)(hi - lo), off + n, kh, kl) - off);
 }
 
-// lower_bound_key of one key (kh, kl) in G lists at once (lists[g], skipped
+// lower_bound_key of G keys (kh[g], kl[g]) in G lists (lists[g], skipped
 // where on[g] is false), the G searches in lockstep so that G loads are in
 // flight per lane.  Each search halves without branches (the probe picks the
 // half, the length shrinks by the same amount whatever the outcome), so lanes
 // searching lists of one length run the same steps: the fence points of the
-// list (first word >= kh & kFenceMask), the bracket, then the first entry of the bracket
-// whose key is >= (kh, kl).  pos[g] is list-relative.  Entry indexes fit 32
+// list (first word >= kh[g] & kFenceMask), the bracket, then the first entry of the
+// bracket whose key is >= (kh[g], kl[g]).  pos[g] is list-relative.  Entry indexes fit 32
 // bits (an index holds fewer than 2^32 entries).
 template <int G>
 __device__ __forceinline__ void lower_bound_lists(const IndexView& ix, const uint32_t (&lists)[G],
-                                                  const bool (&on)[G], uint64_t kh, uint64_t kl,
-                                                  uint32_t (&pos)[G]) {
+                                                  const bool (&on)[G], const uint64_t (&kh)[G],
+                                                  const uint64_t (&kl)[G], uint32_t (&pos)[G]) {
     if (!ix.fence) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             if (!on[g]) continue;
             const uint64_t off = ix.list_off[lists[g]];
             pos[g] = lower_bound_key(ix, lists[g], off,
-                                     (uint32_t)(ix.list_off[lists[g] + 1] - off), kh, kl);
+                                     (uint32_t)(ix.list_off[lists[g] + 1] - off), kh[g], kl[g]);
         }
         return;
     }
-    const uint64_t pk = kh & kFenceMask;
+    uint64_t pk[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) pk[g] = kh[g] & kFenceMask;
     uint32_t off[G], end[G], base[G], len[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -269,7 +271,7 @@ __device__ __forceinline__ void lower_bound_lists(const IndexView& ix, const uin
         for (int g = 0; g < G; ++g) {
             if (len[g] <= 1) continue;
             const uint32_t half = len[g] >> 1;
-            base[g] += f[g] < pk ? half : 0u;
+            base[g] += f[g] < pk[g] ? half : 0u;
             len[g] -= half;
         }
     }
@@ -280,7 +282,7 @@ __device__ __forceinline__ void lower_bound_lists(const IndexView& ix, const uin
     for (int g = 0; g < G; ++g) {
         const bool one = len[g] == 1 && HC_IN_BOUNDS(kSiteSearch, base[g], ix.fence_len);
         const uint64_t fb = one ? __ldg(ix.fence + base[g]) : 0ull;
-        jl[g] = base[g] + (one && fb < pk ? 1u : 0u);
+        jl[g] = base[g] + (one && fb < pk[g] ? 1u : 0u);
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -296,7 +298,7 @@ __device__ __forceinline__ void lower_bound_lists(const IndexView& ix, const uin
         const uint32_t lo = jl[g] > ja ? ((jl[g] - 1) << kFenceShift) + 1 : off[g];
         uint32_t hi = end[g];
         if (jl[g] < jbg) {
-            if (fj[g] > pk) {
+            if (fj[g] > pk[g]) {
                 hi = jl[g] << kFenceShift;
             } else {
                 // fence points tying pk: the first one above it ends the bracket
@@ -305,7 +307,7 @@ __device__ __forceinline__ void lower_bound_lists(const IndexView& ix, const uin
                     const uint32_t step = cnt >> 1;
                     const uint32_t mid = ju + step;
                     if (!HC_IN_BOUNDS(kSiteSearch, mid, ix.fence_len)) break;
-                    if (__ldg(ix.fence + mid) <= pk) {
+                    if (__ldg(ix.fence + mid) <= pk[g]) {
                         ju = mid + 1;
                         cnt -= step + 1;
                     } else {
@@ -336,8 +338,8 @@ __device__ __forceinline__ void lower_bound_lists(const IndexView& ix, const uin
         for (int g = 0; g < G; ++g) {
             if (len[g] <= 1) continue;
             const uint32_t half = len[g] >> 1;
-            bool less = h[g] < kh;
-            if (h[g] == kh) less = entry_key_lo(ix, lists[g], base[g] + half - 1) < kl;
+            bool less = h[g] < kh[g];
+            if (h[g] == kh[g]) less = entry_key_lo(ix, lists[g], base[g] + half - 1) < kl[g];
             base[g] += less ? half : 0u;
             len[g] -= half;
         }
@@ -347,8 +349,8 @@ __device__ __forceinline__ void lower_bound_lists(const IndexView& ix, const uin
         uint32_t at = base[g];
         if (len[g] == 1 && HC_IN_BOUNDS(kSiteSearch, at, end[g])) {
             const uint64_t h = __ldg(ix.keys_hi + at);
-            bool less = h < kh;
-            if (h == kh) less = entry_key_lo(ix, lists[g], at) < kl;
+            bool less = h < kh[g];
+            if (h == kh[g]) less = entry_key_lo(ix, lists[g], at) < kl[g];
             at += less ? 1u : 0u;
         }
         if (on[g]) pos[g] = at - off[g];

@@ -151,52 +151,97 @@ __device__ __forceinline__ void store_group(uint32_t* p, const uint32_t (&at)[G]
     }
 }
 
+// Queries a lane of batch_positions_kernel takes: kBatchILP searches side by
+// side are kBatchILP partitions of one query (three partitions or more: the
+// last group may be partial), or the partitions of four queries (one
+// partition) or of two (two partitions).
+__host__ __device__ __forceinline__ uint32_t batch_queries_per_lane(uint32_t parts) {
+    return parts == 1 ? 4u : (parts == 2 ? 2u : 1u);
+}
+static_assert(kBatchILP == 4, "queries per lane assume four searches side by side");
+
 // K3 for a whole batch.  Warp w takes curve c = w / tiles and tile t = w %
-// tiles: the 32 queries at ranks 32 t .. 32 t + 31 of curve c's key order.
-// Each lane searches its query's curve-c key in list j * curves + c of every
+// tiles: the 32 qpl queries at ranks 32 qpl t .. of curve c's key order, lane
+// l the ranks 32 qpl t + 32 u + l (u < qpl, qpl queries per lane).  Each lane
+// searches its queries' curve-c keys in list j * curves + c of every
 // partition j and writes the position to pos[query][c * partitions + j].  The
-// 32 keys of a warp are neighbours on curve c, so the lanes' probes fall on
-// the same few lines (one request serves many lanes) where lanes of a
+// 32 keys of a warp's round are neighbours on curve c, so the lanes' probes
+// fall on the same few lines (one request serves many lanes) where lanes of a
 // per-query warp would each probe a different list.
+template <int QPL>   // batch_queries_per_lane(partitions)
 __global__ void __launch_bounds__(256) batch_positions_kernel(IndexView ix, uint32_t nq,
                                                               const uint32_t* __restrict__ order,
                                                               const uint64_t* __restrict__ qhi,
                                                               const uint64_t* __restrict__ qlo,
                                                               uint32_t* __restrict__ pos) {
+    constexpr int G = kBatchILP;
+    constexpr uint32_t qpl = QPL;
     const int lane = threadIdx.x & 31;
     const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t curves = ix.P.curves, tiles = (nq + 31) / 32;
+    const uint32_t curves = ix.P.curves, parts = ix.lists / curves;
+    const uint32_t span = 32 * qpl;
+    const uint32_t tiles = (nq + span - 1) / span;
     if (w >= (uint64_t)tiles * curves) return;
     const uint32_t c = (uint32_t)(w / tiles), t = (uint32_t)(w % tiles);
-    const uint32_t r = t * 32 + (uint32_t)lane;
-    bool live = r < nq;
-    uint32_t qi = live ? __ldg(order + (size_t)c * nq + r) : 0u;
-    if (live && !HC_IN_BOUNDS(kSiteQuery, qi, nq)) {
-        live = false;
-        qi = 0;
-    }
-    // lanes past the batch search with query 0's key and write nothing
-    const uint64_t kh = __ldg(qhi + (size_t)c * nq + qi), kl = __ldg(qlo + (size_t)c * nq + qi);
-    const uint32_t parts = ix.lists / curves;
-    uint32_t* out = pos + (size_t)qi * ix.lists + (size_t)c * parts;
-    // kBatchILP partitions at a time: their searches share the key
-    for (uint32_t j0 = 0; j0 < parts; j0 += kBatchILP) {
-        uint32_t lists[kBatchILP], at[kBatchILP];
-        bool on[kBatchILP];
+    // the lane's queries; lanes past the batch search with query 0's key and
+    // write nothing
+    uint32_t qi[QPL];
+    bool live[QPL];
+    uint64_t kh[QPL], kl[QPL];
 #pragma unroll
-        for (int g = 0; g < kBatchILP; ++g) {
+    for (int u = 0; u < QPL; ++u) {
+        const uint32_t r = t * span + (uint32_t)u * 32 + (uint32_t)lane;
+        live[u] = r < nq;
+        qi[u] = live[u] ? __ldg(order + (size_t)c * nq + r) : 0u;
+        if (live[u] && !HC_IN_BOUNDS(kSiteQuery, qi[u], nq)) {
+            live[u] = false;
+            qi[u] = 0;
+        }
+        kh[u] = __ldg(qhi + (size_t)c * nq + qi[u]);
+        kl[u] = __ldg(qlo + (size_t)c * nq + qi[u]);
+    }
+    uint32_t lists[G], at[G];
+    bool on[G];
+    uint64_t gh[G], gl[G];
+    if constexpr (QPL > 1) {
+        // one round: search g is partition g % (G / QPL) of query g / (G / QPL)
+        constexpr int PP = G / QPL;   // partitions (1 or 2)
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            on[g] = live[g / PP];
+            gh[g] = kh[g / PP];
+            gl[g] = kl[g / PP];
+            lists[g] = (uint32_t)(g % PP) * curves + c;
+        }
+        lower_bound_lists<G>(ix, lists, on, gh, gl, at);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (on[g])
+                pos[(size_t)qi[g / PP] * ix.lists + (size_t)c * PP + (uint32_t)(g % PP)] = at[g];
+        return;
+    }
+    uint32_t* out = pos + (size_t)qi[0] * ix.lists + (size_t)c * parts;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        gh[g] = kh[0];
+        gl[g] = kl[0];
+    }
+    // G partitions at a time: their searches share the key
+    for (uint32_t j0 = 0; j0 < parts; j0 += G) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
             on[g] = j0 + g < parts;
             lists[g] = on[g] ? (j0 + g) * curves + c : 0u;
         }
-        lower_bound_lists<kBatchILP>(ix, lists, on, kh, kl, at);
-        if (!live) continue;
-        if (parts % kBatchILP == 0) {
+        lower_bound_lists<G>(ix, lists, on, gh, gl, at);
+        if (!live[0]) continue;
+        if (parts % G == 0) {
             // whole groups: one vector store (the row offset is a multiple
             // of the group since partitions are)
             store_group(out + j0, at);
         } else {
 #pragma unroll
-            for (int g = 0; g < kBatchILP; ++g)
+            for (int g = 0; g < G; ++g)
                 if (on[g]) out[j0 + g] = at[g];
         }
     }
@@ -273,10 +318,16 @@ cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, u
 cudaError_t launch_batch_positions(const IndexView& ix, uint32_t nq, const uint32_t* order,
                                    const uint64_t* qhi, const uint64_t* qlo, uint32_t* pos,
                                    cudaStream_t s) {
-    const uint64_t warps = (uint64_t)((nq + 31) / 32) * ix.P.curves;
+    const uint32_t qpl = batch_queries_per_lane(ix.lists / ix.P.curves), span = 32 * qpl;
+    const uint64_t warps = (uint64_t)((nq + span - 1) / span) * ix.P.curves;
     if (warps == 0) return cudaSuccess;
-    batch_positions_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(ix, nq, order, qhi, qlo,
-                                                                       pos);
+    const unsigned blocks = (unsigned)((warps + 7) / 8);
+    if (qpl == 4)
+        batch_positions_kernel<4><<<blocks, 256, 0, s>>>(ix, nq, order, qhi, qlo, pos);
+    else if (qpl == 2)
+        batch_positions_kernel<2><<<blocks, 256, 0, s>>>(ix, nq, order, qhi, qlo, pos);
+    else
+        batch_positions_kernel<1><<<blocks, 256, 0, s>>>(ix, nq, order, qhi, qlo, pos);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -390,11 +390,13 @@ def test_query_ordered_other_key_widths(hc, d, curves, m):
 
 @pytest.mark.parametrize("parts,curves,m,nq", [(8, 8, 16, 1000), (32, 8, 16, 333),
                                                 (16, 16, 8, 65), (256, 1, 16, 40),
-                                                (3, 32, 4, 97)])
+                                                (3, 32, 4, 97), (2, 8, 16, 501),
+                                                (1, 8, 16, 1000), (1, 3, 16, 130)])
 def test_query_ordered_batch_search_many_lists(hc, parts, curves, m, nq):
     """The ordered path's batch search (a warp per 32 neighbouring keys of one
-    curve, over that curve's list in every partition) gives the positions of
-    Algorithm 2: the walk over up to 256 lists equals the oracle's search,
+    curve, over that curve's list in every partition; with one or two
+    partitions a lane takes four or two queries) gives the positions of
+    Algorithm 2: the walk over 3 to 256 lists equals the oracle's search,
     with batches that end in a partial warp."""
     db, q = make_case(20011, nq, seed=parts * 7 + curves)
     idx = hc.hc_build(dev(db), curves=curves, dims_per_curve=m, partitions=parts)
