@@ -374,17 +374,25 @@ def test_free_async_on_streams(hc):
         assert torch.equal(ids, ref)
 
 
-@pytest.mark.parametrize("d,curves,m", [(64, 10, 6), (128, 12, 10), (256, 16, 16)])
-def test_query_ordered_other_key_widths(hc, d, curves, m):
-    """Order keys from 48-, 80- and 128-bit extended-keys: any order gives
-    the same results."""
+@pytest.mark.parametrize("d,curves,m,parts", [(64, 10, 6, 1), (128, 12, 10, 1), (256, 16, 16, 1),
+                                               (64, 10, 6, 2), (128, 12, 10, 3), (64, 4, 16, 5)])
+def test_query_ordered_other_key_widths(hc, d, curves, m, parts):
+    """Order keys from 48-, 80- and 128-bit extended-keys (indexes that keep
+    low words; their fence is written after the sort), on one to five
+    partitions: the ordered path gives hc_query's results, and the oracle's
+    on the partitioned cases."""
     import torch
-    db, q = make_case(9001, 333, d=d, seed=d + m)
-    idx = hc.hc_build(dev(db), curves=curves, dims_per_curve=m)
+    db, q = make_case(9001, 333, d=d, seed=d + m + parts)
+    idx = hc.hc_build(dev(db), curves=curves, dims_per_curve=m, partitions=parts)
     ids_a, dist_a = hc.hc_query(idx, dev(q), 10, 25)
     ids_b, dist_b = hc.hc_query_ordered(idx, dev(q), 10, 25)
     sync()
     assert torch.equal(ids_a, ids_b) and torch.equal(dist_a, dist_b)
+    if parts > 1:
+        oidx = O.build(db, curves=curves, m=m, ell=parts)
+        rids, rdist = O.search(oidx, db, q, 10, 25)
+        assert np.array_equal(ids_b.cpu().numpy(), rids)
+        assert np.array_equal(dist_b.cpu().numpy(), O.int32_dist(rdist))
     idx.free()
 
 
