@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) batch_positions_kernel(IndexView ix, uint
     const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t curves = ix.P.curves, parts = ix.lists / curves;
     const uint32_t span = 32 * qpl;
-    const uint32_t tiles = (nq + span - 1) / span;
+    const uint32_t tiles = (uint32_t)(((uint64_t)nq + span - 1) / span);
     if (w >= (uint64_t)tiles * curves) return;
     const uint32_t c = (uint32_t)(w / tiles), t = (uint32_t)(w % tiles);
     // the lane's queries; lanes past the batch search with query 0's key and
@@ -271,7 +271,7 @@ template <bool F32, int LPR, int KR>
 struct QueryLaunch {
     template <bool STAGED>
     static cudaError_t go(const QueryArgs& a, size_t smem, cudaStream_t s) {
-        const unsigned blocks = (a.nq + kQWarps - 1) / kQWarps;
+        const unsigned blocks = (unsigned)(((uint64_t)a.nq + kQWarps - 1) / kQWarps);
         if (STAGED) {
             cudaError_t e = cudaFuncSetAttribute(query_kernel<F32, LPR, KR, STAGED>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -309,7 +309,7 @@ cudaError_t launch_query(const IndexView& ix, const void* q, uint32_t nq, uint32
 cudaError_t launch_order_keys(const IndexView& ix, const void* q, uint32_t nq, uint32_t ncurves,
                               uint64_t* keys, uint64_t* qhi, uint64_t* qlo, cudaStream_t s) {
     if (nq == 0 || ncurves == 0) return cudaSuccess;
-    order_keys_kernel<<<(nq + 255) / 256, 256, 0, s>>>(ix, static_cast<const uint8_t*>(q), nq,
+    order_keys_kernel<<<(unsigned)(((uint64_t)nq + 255) / 256), 256, 0, s>>>(ix, static_cast<const uint8_t*>(q), nq,
                                                        ncurves, keys, qhi, qlo);
     count_launches(1);
     return cudaGetLastError();
@@ -319,7 +319,7 @@ cudaError_t launch_batch_positions(const IndexView& ix, uint32_t nq, const uint3
                                    const uint64_t* qhi, const uint64_t* qlo, uint32_t* pos,
                                    cudaStream_t s) {
     const uint32_t qpl = batch_queries_per_lane(ix.lists / ix.P.curves), span = 32 * qpl;
-    const uint64_t warps = (uint64_t)((nq + span - 1) / span) * ix.P.curves;
+    const uint64_t warps = (((uint64_t)nq + span - 1) / span) * ix.P.curves;
     if (warps == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((warps + 7) / 8);
     if (qpl == 4)
@@ -349,7 +349,7 @@ cudaError_t launch_positions(const IndexView& ix, const void* q, uint32_t nq, in
                              cudaStream_t s) {
     if (nq == 0) return cudaSuccess;
     QueryArgs a{ix, q, nq, 1, 0, nullptr, nullptr, pos, nullptr, nullptr, nullptr};
-    const unsigned blocks = (nq + kQWarps - 1) / kQWarps;
+    const unsigned blocks = (unsigned)(((uint64_t)nq + kQWarps - 1) / kQWarps);
     positions_kernel<<<blocks, kQWarps * 32, sizeof(uint32_t) * kQWarps * ix.lists, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
