@@ -306,8 +306,17 @@ int build_index(hc_index* x, cudaStream_t s) {
     uint64_t* id_base_dev = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + key_bytes);
     void* sort_scratch = static_cast<char*>(scratch) + key_bytes + base_bytes;
 
+    sp.hi = hi0;
+    sp.lo = lo0;
+    sp.ids = nullptr;
+    sp.id_base_dev = id_base_dev;
+    sp.rows = RowKeys{x->db, x->row_bytes, view_of(x).P};
+    // the key pass also leaves the first radix pass's digit bytes, so that
+    // pass's histogram reads bytes instead of words
+    const FirstDigits fd = sort_first_digits(sp, sort_scratch);
+    sp.first_digits_ready = fd.buf != nullptr;
     BuildKeysArgs ka{x->db, P.n, x->row_bytes, view_of(x).P, parts, x->list_off_dev, hi0, lo0,
-                     nullptr};
+                     nullptr, fd.buf, fd.shift};
     {
         TraceRange tk("keys");
         rc = status_of(launch_build_keys(ka, s));
@@ -315,11 +324,6 @@ int build_index(hc_index* x, cudaStream_t s) {
     if (rc == HC_OK)
         rc = status_of(upload_small(id_base_dev, id_base.data(), sizeof(uint64_t) * x->lists, s));
     if (rc == HC_OK) {
-        sp.hi = hi0;
-        sp.lo = lo0;
-        sp.ids = nullptr;
-        sp.id_base_dev = id_base_dev;
-        sp.rows = RowKeys{x->db, x->row_bytes, view_of(x).P};
         TraceRange ts("sort");
         rc = sort_segments(sp, sort_scratch, s);
     }

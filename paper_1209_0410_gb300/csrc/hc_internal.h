@@ -31,6 +31,11 @@ struct BuildKeysArgs {
     uint64_t* hi;
     uint64_t* lo;
     uint32_t* ids;             // may be null: ids are then implied by the slot
+    // may be null: digits[g] = (hi[g] >> digit_shift) & 0xFF, the first radix
+    // pass's digit of every key (sort_first_digits), so that its histogram
+    // reads bytes instead of words
+    uint8_t* digits;
+    int digit_shift;
 };
 cudaError_t launch_build_keys(const BuildKeysArgs& a, cudaStream_t s);
 
@@ -83,11 +88,23 @@ struct SortProblem {
     // bits): the last radix pass writes the ids and nothing is gathered;
     // out_hi and out_lo serve as scratch and are left undefined
     bool ids_only = false;
+    // high-word-first path with affine ids only: the caller wrote the first
+    // pass's digit bytes into sort_first_digits(...).buf before the sort
+    bool first_digits_ready = false;
 };
 // Scratch bytes the sort needs for this problem (queried before allocating).
 size_t sort_scratch_bytes(const SortProblem& p);
 // Enqueues the whole sort on s using the given scratch (>= sort_scratch_bytes).
 int sort_segments(const SortProblem& p, void* scratch, cudaStream_t s);
+// Where a producer of the keys may leave the first radix pass's digit of
+// every record (one byte at the record's position) for the high-word-first
+// path with affine ids: buf (inside scratch) and the digit's shift in the high
+// word; buf is null for problems that take another path.
+struct FirstDigits {
+    uint8_t* buf = nullptr;
+    int shift = 0;
+};
+FirstDigits sort_first_digits(const SortProblem& p, void* scratch);
 
 // Small host tables written to device memory by a kernel that takes them
 // as a by-value parameter, so that no pageable copy (and its implicit

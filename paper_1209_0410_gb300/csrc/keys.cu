@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
                     a.hi[g] = hi[t];
                     if (a.lo) a.lo[g] = lo[t];
                     if (a.ids) a.ids[g] = (uint32_t)r;
+                    if (a.digits) a.digits[g] = (uint8_t)(hi[t] >> a.digit_shift);
                 }
             }
         }
@@ -45,6 +46,7 @@ __global__ void __launch_bounds__(256) build_keys_kernel(BuildKeysArgs a) {
             a.hi[g] = hi;
             if (a.lo) a.lo[g] = lo;
             if (a.ids) a.ids[g] = (uint32_t)r;
+            if (a.digits) a.digits[g] = (uint8_t)(hi >> a.digit_shift);
         }
     }
 }

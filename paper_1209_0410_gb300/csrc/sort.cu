@@ -1051,6 +1051,18 @@ unsigned grid_stride_blocks(uint64_t work) {
 
 size_t sort_scratch_bytes(const SortProblem& p) { return make_layout(p).bytes; }
 
+FirstDigits sort_first_digits(const SortProblem& p, void* scratch) {
+    FirstDigits f;
+    const int digits = (int)((p.key_bits + 7) / 8);
+    const int hi_passes = std::max(digits - 8, 0);
+    const bool in_place = p.lo == nullptr && p.id_base_dev != nullptr;
+    if (!in_place || hi_passes == 0 || p.seg_off.size() < 2) return f;
+    const int skip = (p.hi_skip > 0 && hi_passes > p.hi_skip) ? p.hi_skip : 0;
+    f.buf = static_cast<uint8_t*>(scratch) + make_layout(p).off_digits;
+    f.shift = ((8 + skip) & 7) * 8;
+    return f;
+}
+
 namespace {
 struct SmallBlock {
     uint64_t w[kMaxParamWords];
@@ -1134,8 +1146,9 @@ int sort_body(const SortProblem& p, void* scratch, cudaStream_t s, bool& fenced)
             const bool last = t + 1 == 8 + hi_passes;
             uint32_t* pd = (last && in_place) ? p.out_ids : pbuf_of(pa, pb, pn);
             const bool first = t == 8 + skip;
-            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cw, first ? nullptr : dgt, shift, L.nseg,
-                                                      segs, counts);
+            // the first pass reads words unless the key producer left its digits
+            const uint8_t* hd = first && !p.first_digits_ready ? nullptr : dgt;
+            hist_kernel<<<L.ntiles, kThreads, 0, s>>>(cw, hd, shift, L.nseg, segs, counts);
             scan_kernel<<<scan_grid, kScanThreads, 0, s>>>(segs, counts, totals);
             scatter_kernel<<<L.ntiles, kSThreads, dyn_smem, s>>>(
                 cw, cp, wb[wn], pd, shift, L.nseg, segs, counts, totals,
