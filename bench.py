@@ -228,8 +228,8 @@ def build_bytes(n, row_bytes, curves, passes=BUILD_PASSES):
     read once, c n (key, id) records of 20 bytes written, and every radix pass
     reading and writing every record.
     kernel: what the build's kernels move -- the key pass (rows in, 8-byte high
-    words out); per pass the histogram (the words on the first pass, one digit
-    byte after), the digit counts (written, scanned, read back: one 4-byte
+    words and the first pass's digit byte out); per pass the histogram (one
+    digit byte per record), the digit counts (written, scanned, read back: one 4-byte
     word per digit and 4096-record tile, four times), and the scatter (word
     and position in -- the first pass derives positions -- word and position
     out plus the next pass's digit byte; the last pass writes ids in place of
@@ -239,10 +239,10 @@ def build_bytes(n, row_bytes, curves, passes=BUILD_PASSES):
     r = curves * n
     algorithmic = n * row_bytes + r * 20 + passes * 2 * r * 20
     counts = 4 * 4 * 256 * (r / 4096.0)
-    kernel = n * row_bytes + r * 8                      # key pass
+    kernel = n * row_bytes + r * 9                      # key pass: words + first digits
     for t in range(passes):
         first, last = t == 0, t == passes - 1
-        kernel += r * (8 if first else 1) + counts      # histogram + counts
+        kernel += r * 1 + counts                        # histogram + counts
         kernel += r * (8 if first else 12)              # scatter reads
         kernel += r * (12 if last else 13)              # scatter writes
     kernel += r * 12                                    # run fix-up

@@ -80,8 +80,8 @@ def test_build_bytes_counts_every_pass():
     r = c * n
     assert alg == n * row + 20 * r + 3 * 40 * r
     counts = 16 * 256 * r / 4096
-    keys = n * row + 8 * r
-    p1 = 8 * r + counts + 8 * r + 13 * r
+    keys = n * row + 9 * r
+    p1 = 1 * r + counts + 8 * r + 13 * r
     p2 = 1 * r + counts + 12 * r + 13 * r
     p3 = 1 * r + counts + 12 * r + 12 * r
     assert ker == pytest.approx(keys + p1 + p2 + p3 + 12 * r + 0.5 * r)
