@@ -6,7 +6,12 @@
 //   K1  lanes c < curves compute the query's extended-key on curve c;
 //   K3  lanes L < lists run lower_bound in list L (128-bit compares; the low
 //       word is consulted only when the high words tie, recomputed from the
-//       entry's row when the index keeps high words only);
+//       entry's row when the index keeps high words only), starting on the
+//       index's fence of every 16th high word.  For hc_query_ordered, K1 and
+//       K3 run before the walk as passes over the whole batch instead
+//       (order_keys_kernel: every curve's key of every query; a sort by each
+//       curve's key; batch_positions_kernel: a warp per 32 neighbouring keys
+//       of one curve), and the walk reads the positions;
 //   K4  the windows [max(0,pos-p), min(n,pos+p)) are walked 32 entries at a
 //       time: the 32 ids are one load, then each row is read as 16-byte
 //       vectors by LPR lanes (LPR = 8 for 128-byte uint8 rows: four rows per
@@ -134,8 +139,8 @@ __global__ void __launch_bounds__(256) order_keys_kernel(IndexView ix, const uin
     }
 }
 
-// partitions a lane of batch_positions_kernel searches side by side (1, 2
-// and 8 measured slower on 32 partitions; 4 keeps the kernel at 76 registers)
+// searches a lane of batch_positions_kernel runs side by side (1, 2 and 8
+// measured slower on 32 partitions)
 constexpr int kBatchILP = 4;
 
 // at[0 .. G) to p[0 .. G), p aligned to 4 G bytes
