@@ -471,8 +471,9 @@ __global__ void __launch_bounds__(kFindWarps * 32) find_runs_kernel(
     const bool tile_after = lt + 1 < si.ntiles;
     uint32_t found = 0;
     // fence words of the warp's 32 x 16 records: word l (lane l) is the high
-    // word at wpos0 + 16 l, the l-th position of the warp that is a multiple of
-    // 16; chunk c holds words 2c and 2c + 1 at its offsets a0 and a0 + 16
+    // word at wbeg + a0 + 16 l, the l-th position of the warp that is a
+    // multiple of 16; chunk c holds words 2c and 2c + 1 at its offsets a0 and
+    // a0 + 16
     const uint64_t wbeg = start + (uint64_t)warp * kFindChunks * 32;
     const uint32_t a0 = (uint32_t)((16 - (wbeg & 15)) & 15);
     uint64_t fw = 0;
