@@ -300,17 +300,20 @@ def test_build_long_runs_of_equal_keys(hc, parts, copies):
 
 @pytest.mark.parametrize("n", [1, 2, 31, 33, 70])
 def test_query_tiny_databases(hc, n):
-    """Lists shorter than one 32-entry step: the packed walk fills steps from
-    several windows and pads the top-k when fewer than k rows exist."""
+    """Lists shorter than one 32-entry step (and than the 16 entries of one
+    fence point, which some lists then lack): the packed walk fills steps
+    from several windows and pads the top-k when fewer than k rows exist;
+    the ordered path's batch search agrees."""
     db, q = make_case(n, 40, seed=n + 11)
     idx = hc.hc_build(dev(db))
     oidx = O.build(db, curves=8, m=16)
     for k, p in [(10, 2), (10, 100), (1, 1), (128, 40)]:
-        ids, dist = hc.hc_query(idx, dev(q), k, p)
-        sync()
         rids, rdist = O.search(oidx, db, q, k, p)
-        assert np.array_equal(ids.cpu().numpy(), rids)
-        assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
+        for query in (hc.hc_query, hc.hc_query_ordered):
+            ids, dist = query(idx, dev(q), k, p)
+            sync()
+            assert np.array_equal(ids.cpu().numpy(), rids)
+            assert np.array_equal(dist.cpu().numpy(), O.int32_dist(rdist))
     idx.free()
 
 
