@@ -224,7 +224,7 @@ E2E_RUNS = 5       # timed runs of the end-to-end pipeline; the line reports the
 def build_bytes(n, row_bytes, curves, passes=BUILD_PASSES):
     """Bytes of one index build of n rows and `curves` lists.
 
-    algorithmic: the method's own traffic as the survey counts it -- the rows
+    algorithmic: the method's own traffic, counted by record -- the rows
     read once, c n (key, id) records of 20 bytes written, and every radix pass
     reading and writing every record.
     kernel: what the build's kernels move -- the key pass (rows in, 8-byte high

@@ -72,7 +72,7 @@ def test_fixed_recall_point_picks_smallest_depth_reaching_reference():
 
 
 def test_build_bytes_counts_every_pass():
-    """The survey's build bytes (rows once, 20-byte records written, every
+    """The algorithmic build bytes (rows once, 20-byte records written, every
     pass reading and writing every record) and the kernels' bytes, counted
     here pass by pass for a small case."""
     n, row, c = 1000, 128, 8
