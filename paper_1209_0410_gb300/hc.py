@@ -356,9 +356,10 @@ def hc_query_ordered_workspace(index, nq):
 
 
 def hc_query_ordered(index, q, k, p, out_ids=None, out_dist=None, workspace=None, stream=None):
-    """hc_query answering the queries in curve-0 key order (results identical);
-    workspace: a CUDA uint8 tensor of at least
-    hc_query_ordered_workspace(index, nq) bytes (allocated here when None)."""
+    """hc_query answering the queries in curve-0 key order, their lower_bound
+    positions found first by one batch pass (results identical); workspace: a
+    CUDA uint8 tensor of at least hc_query_ordered_workspace(index, nq) bytes
+    (allocated here when None)."""
     nq = q.shape[0]
     if out_ids is None:
         out_ids = torch.empty((nq, k), dtype=torch.int32, device=q.device)
